@@ -1,0 +1,332 @@
+"""Seeded synthetic workloads: mesh descriptors, physical constants, initial states, random vectors.
+
+This module is the one place both the CUDA path and the CPU oracle take their inputs from. It holds
+no arithmetic of the discretisation: no basis, quadrature, geometry, flux or residual. It only
+states *which problem* is solved (the domain description, the nondimensional numbers of the model in
+Sec. 2.4, the base atmosphere and the seeded perturbations) and draws random numbers.
+
+State functions take node coordinates as an argument, so each side evaluates them on its own mesh
+(the oracle on its nodes for parity tests; the benchmark on the library's nodes).
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) used as a counter-based generator: value(seed, i) = mix(seed + (i+1)*phi).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict
+
+import numpy as np
+
+# ----------------------------------------------------------------------------------------------
+# SI constants of the thermosphere workloads (Sec. 2; reference values at the lower boundary, Sec. 2.4)
+# ----------------------------------------------------------------------------------------------
+K_B = 1.380649e-23          # Boltzmann constant [J/K]
+AMU = 1.66053906660e-27     # atomic mass unit [kg]
+R_EARTH = 6371.0e3          # Earth radius [m]
+G_SURFACE = 9.81            # surface gravity of the workloads, g = 9.81 (R_E / r)^2 [m/s^2]
+OMEGA_EARTH = 7.292e-5      # rotation rate [rad/s]
+GAMMA = 5.0 / 3.0           # ratio of specific heats (Sec. 2.1)
+
+# boundary kinds (same integer codes as include/dg.h)
+BC_PERIODIC = 0
+BC_WALL = 1
+BC_OUTFLOW = 2
+
+KIND_BOX = 0
+KIND_SHELL = 1
+
+
+@dataclass
+class MeshDesc:
+    """Problem description handed to both the library (dg_mesh_desc) and the oracle.
+
+    Box: [0,lx]x[0,ly]x[0,lz], nx*ny*nz hexahedra, periodic in x and y; the z ends carry
+    bc_lo / bc_hi. Shell: cubed sphere, 6 panels of nx*nx elements, nz radial layers between
+    r_inner and r_outer (nondimensional), first layer height h_first (geometric growth; <= 0 means
+    uniform layers); bc_lo is the inner sphere, bc_hi the outer one.
+    """
+    kind: int = KIND_BOX
+    p: int = 2
+    nx: int = 4
+    ny: int = 4
+    nz: int = 4
+    lx: float = 1.0
+    ly: float = 1.0
+    lz: float = 1.0
+    r_inner: float = 0.0
+    r_outer: float = 0.0
+    h_first: float = 0.0
+    bc_lo: int = BC_PERIODIC
+    bc_hi: int = BC_PERIODIC
+    # nondimensional physics (Eq. fluxSWNondimensional, Eq. nondimensional)
+    gamma: float = GAMMA
+    grashof: float = 100.0 ** 2 / GAMMA
+    prandtl: float = 0.7
+    mass: float = 1.0           # m* (molecular mass / m_O); c_v* = 1/m*
+    visc_exp: float = 0.0       # mu* = kappa* = T*^visc_exp (0: constant)
+    lambda0: float = 1.0        # sigma_c = lambda0 * I
+    t_wall: float = 1.0         # isothermal wall temperature T*
+    gravity_kind: int = 0       # 0: constant vector gvec; 1: radial, g* = -(g_r0/|r|)^2 r/|r|
+    gvec: tuple = (0.0, 0.0, -1.0)
+    g_r0: float = 0.0
+    omega: tuple = (0.0, 0.0, 0.0)  # omega* (unit rotation axis times omega/omega_0)
+    froude: float = 0.0
+    euv: int = 0                # Gaussian sub-solar heating on/off
+    euv_amp: float = 0.0        # peak heating, nondimensional (q H0 / (rho0 c_v0 T0 a0))
+    euv_sigma: float = 0.0      # zenith-angle standard deviation [rad]
+    euv_r_peak: float = 0.0     # radius of the heating peak (nondimensional)
+    euv_width: float = 0.0      # vertical half width at half maximum (nondimensional)
+    euv_omega_t: float = 0.0    # rotation angle of the sub-solar point per unit nondimensional time
+
+    def as_dict(self):
+        return asdict(self)
+
+    @property
+    def n_elem(self) -> int:
+        if self.kind == KIND_BOX:
+            return self.nx * self.ny * self.nz
+        return 6 * self.nx * self.nx * self.nz
+
+    @property
+    def n_p(self) -> int:
+        return (self.p + 1) ** 3
+
+    @property
+    def n_dof(self) -> int:
+        return 5 * self.n_elem * self.n_p
+
+
+@dataclass
+class Reference:
+    """Reference scales of Sec. 2.4 (lower-boundary values) for the shell workloads."""
+    T0: float
+    rho0: float
+    m_O: float
+    g0: float
+    H0: float
+    a0: float
+    t0: float
+    mu0: float
+    kappa0: float
+    Re: float
+    Gr: float
+    Pr: float
+    Fr: float
+    cv0: float
+
+
+def shell_reference(T0=200.0, rho0=5.0e-7, h0=100.0e3) -> Reference:
+    """Reference quantities at the lower boundary (Sec. 2.4).
+
+    mu_0 and kappa_0 follow the nominal molecular laws of Sec. 2.2 evaluated in SI units for pure
+    atomic oxygen at T0: mu_m = 6.5e-4 sqrt(T m / k), kappa_m = alpha_O T^0.69 with alpha_O = 5.6e-4.
+    """
+    m_O = 16.0 * AMU
+    g0 = G_SURFACE * (R_EARTH / (R_EARTH + h0)) ** 2
+    H0 = K_B * T0 / (m_O * g0)
+    a0 = math.sqrt(GAMMA * K_B * T0 / m_O)
+    mu0 = 6.5e-4 * math.sqrt(T0 * m_O / K_B)
+    kappa0 = 5.6e-4 * T0 ** 0.69
+    cv0 = K_B / ((GAMMA - 1.0) * m_O)
+    cp0 = GAMMA * cv0
+    Gr = g0 * H0 ** 3 / (mu0 / rho0) ** 2
+    Re = rho0 * a0 * H0 / mu0
+    Pr = mu0 * cp0 / kappa0
+    Fr = math.sqrt(OMEGA_EARTH ** 2 * H0 / g0)
+    return Reference(T0=T0, rho0=rho0, m_O=m_O, g0=g0, H0=H0, a0=a0, t0=H0 / a0, mu0=mu0,
+                     kappa0=kappa0, Re=Re, Gr=Gr, Pr=Pr, Fr=Fr, cv0=cv0)
+
+
+# ----------------------------------------------------------------------------------------------
+# workload descriptors
+# ----------------------------------------------------------------------------------------------
+def box_desc(p=2, n=4, re=100.0, pr=0.7, bc_lo=BC_PERIODIC, bc_hi=BC_PERIODIC, gravity=1.0,
+             visc_exp=0.0, nz=None, lz=1.0) -> MeshDesc:
+    """Periodic unit box with constant gravity along -z (the 4x4x4, p=2 parity workload)."""
+    return MeshDesc(kind=KIND_BOX, p=p, nx=n, ny=n, nz=n if nz is None else nz, lx=1.0, ly=1.0,
+                    lz=lz, bc_lo=bc_lo, bc_hi=bc_hi, grashof=re * re / GAMMA, prandtl=pr,
+                    visc_exp=visc_exp, gvec=(0.0, 0.0, -gravity))
+
+
+def shell_desc(n=16, nr=8, p=4, euv=False, rotation=True, h_first_km=2.5, ref: Reference | None = None,
+               bc_lo=BC_WALL, bc_hi=BC_OUTFLOW) -> MeshDesc:
+    """Cubed-sphere shell 100-600 km (Sec. 3.3) with the nondimensional numbers of Sec. 2.4."""
+    ref = ref or shell_reference()
+    H0 = ref.H0
+    r_in = (R_EARTH + 100.0e3) / H0
+    r_out = (R_EARTH + 600.0e3) / H0
+    d = MeshDesc(kind=KIND_SHELL, p=p, nx=n, ny=n, nz=nr, r_inner=r_in, r_outer=r_out,
+                 h_first=h_first_km * 1.0e3 / H0, bc_lo=bc_lo, bc_hi=bc_hi, grashof=ref.Gr,
+                 prandtl=ref.Pr, mass=1.0, visc_exp=0.69, lambda0=1.0, t_wall=1.0,
+                 gravity_kind=1, gvec=(0.0, 0.0, 0.0), g_r0=r_in,
+                 omega=(0.0, 0.0, 1.0) if rotation else (0.0, 0.0, 0.0),
+                 froude=ref.Fr if rotation else 0.0)
+    if euv:
+        d.euv = 1
+        d.euv_amp = 1.0e-8 * H0 / (ref.rho0 * ref.cv0 * ref.T0 * ref.a0)
+        d.euv_sigma = math.radians(60.0)
+        d.euv_r_peak = (R_EARTH + 300.0e3) / H0
+        d.euv_width = 50.0e3 / H0
+        d.euv_omega_t = OMEGA_EARTH * ref.t0
+    return d
+
+
+CONFIGS = {
+    # name: (descriptor factory, human description)
+    "box4_p2": (lambda: box_desc(p=2, n=4), "periodic unit box 4x4x4, p=2, Re=100, Pr=0.7"),
+    "shell16x8_p4": (lambda: shell_desc(n=16, nr=8, p=4), "cubed-sphere shell 6x16x16x8, p=4"),
+    "shell32x16_p2_euv": (lambda: shell_desc(n=32, nr=16, p=2, euv=True),
+                          "cubed-sphere shell 6x32x32x16, p=2, EUV"),
+    "shell48x16_p3_euv": (lambda: shell_desc(n=48, nr=16, p=3, euv=True),
+                          "cubed-sphere shell 6x48x48x16, p=3, EUV"),
+}
+
+
+# ----------------------------------------------------------------------------------------------
+# SplitMix64 counter-based random numbers
+# ----------------------------------------------------------------------------------------------
+_PHI = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, idx: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for counters idx (uint64 arithmetic wraps modulo 2^64)."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (np.asarray(idx, dtype=np.uint64) + np.uint64(1)) * _PHI
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n doubles in [0,1) from counters offset..offset+n-1 (53 high bits)."""
+    z = splitmix64(seed, np.arange(offset, offset + n, dtype=np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n standard normals by Box-Muller from pairs of SplitMix64 uniforms."""
+    m = (n + 1) // 2
+    u1 = uniform01(seed, m, offset)
+    u2 = uniform01(seed, m, offset + m)
+    rad = np.sqrt(-2.0 * np.log1p(-u1))   # 1 - u1 in (0, 1]
+    z = np.concatenate([rad * np.cos(2.0 * np.pi * u2), rad * np.sin(2.0 * np.pi * u2)])
+    return z[:n]
+
+
+def unit_vector(seed: int, shape) -> np.ndarray:
+    """Seeded N(0,1) vector of the given shape normalised to unit 2-norm."""
+    n = int(np.prod(shape))
+    z = normal(seed, n)
+    return (z / np.sqrt(np.dot(z, z))).reshape(shape)
+
+
+def _wavevectors(kmax=3):
+    ks = []
+    for a in range(-kmax, kmax + 1):
+        for b in range(-kmax, kmax + 1):
+            for c in range(-kmax, kmax + 1):
+                if 0 < a * a + b * b + c * c <= kmax * kmax:
+                    ks.append((a, b, c))
+    return np.array(ks, dtype=np.float64)
+
+
+def fourier_field(seed: int, stream: int, xs: np.ndarray, kmax=3) -> np.ndarray:
+    """Random Fourier sum over integer wavevectors 0 < |k|_2 <= kmax at points xs[..., 3].
+
+    f(x) = sum_k a_k cos(2 pi k.x) + b_k sin(2 pi k.x), a, b ~ U(-1, 1), divided by
+    sum_k (|a_k| + |b_k|) so that |f| <= 1 everywhere. Periodic on the unit cube.
+    """
+    ks = _wavevectors(kmax)
+    nk = ks.shape[0]
+    ab = 2.0 * uniform01(seed, 2 * nk, offset=stream * 4096) - 1.0
+    a, b = ab[:nk], ab[nk:]
+    phase = 2.0 * np.pi * np.tensordot(xs, ks.T, axes=([-1], [0]))
+    f = np.cos(phase) @ a + np.sin(phase) @ b
+    return f / (np.abs(a).sum() + np.abs(b).sum())
+
+
+# ----------------------------------------------------------------------------------------------
+# base atmospheres
+# ----------------------------------------------------------------------------------------------
+def bates_temperature(z_km):
+    """Bates profile T(z) = 1000 - 800 exp(-0.02 (z - 100)) [K], z in km."""
+    return 1000.0 - 800.0 * np.exp(-0.02 * (z_km - 100.0))
+
+
+def bates_hydrostatic(r_m: np.ndarray, ref: Reference, p_points=16):
+    """Density [kg/m^3] and temperature [K] of the Bates atmosphere in hydrostatic balance.
+
+    ln p(r) = ln p0 - int_{R0}^{r} m g(s) / (k_B T(s)) ds with g = 9.81 (R_E/s)^2, integrated by
+    composite Gauss-Legendre between consecutive distinct radii; rho = p m / (k_B T).
+    """
+    R0 = R_EARTH + 100.0e3
+    m = ref.m_O
+    shape = r_m.shape
+    rr = r_m.ravel()
+    key = np.round(rr, 6)
+    uniq, inv = np.unique(key, return_inverse=True)
+    xg, wg = np.polynomial.legendre.leggauss(p_points)
+    edges = np.concatenate([[R0], uniq])
+    lo, hi = edges[:-1], edges[1:]
+    s = 0.5 * (hi - lo)[:, None] * xg[None, :] + 0.5 * (hi + lo)[:, None]
+    integrand = m * G_SURFACE * (R_EARTH / s) ** 2 / (K_B * bates_temperature((s - R_EARTH) / 1.0e3))
+    seg = 0.5 * (hi - lo) * (integrand @ wg)
+    lnp_rel = -np.cumsum(seg)
+    T = bates_temperature((uniq - R_EARTH) / 1.0e3)
+    p0 = ref.rho0 * K_B * ref.T0 / m
+    rho = p0 * np.exp(lnp_rel) * m / (K_B * T)
+    return rho[inv].reshape(shape), T[inv].reshape(shape)
+
+
+# ----------------------------------------------------------------------------------------------
+# initial states on a node array x[N_e][3][N_p]
+# ----------------------------------------------------------------------------------------------
+def pack_state(rho, v, T):
+    """u = (log rho*, sqrt(rho*) v*, sqrt(rho*) T*) in the layout [N_e][5][N_p] (Sec. 2.3)."""
+    sr = np.sqrt(rho)
+    return np.stack([np.log(rho), sr * v[0], sr * v[1], sr * v[2], sr * T], axis=1)
+
+
+def box_state(x: np.ndarray, seed: int = 1, amp=0.01):
+    """Uniform rho = T = 1, v = 0 plus seeded |k| <= 3 Fourier modes of amplitude amp."""
+    xs = np.moveaxis(x, 1, -1)
+    f = [fourier_field(seed, s, xs) for s in range(5)]
+    rho = 1.0 + amp * f[0]
+    T = 1.0 + amp * f[4]
+    v = np.stack([amp * f[1], amp * f[2], amp * f[3]])
+    return pack_state(rho, v, T)
+
+
+def shell_state(x: np.ndarray, desc: MeshDesc, seed: int = 2, ref: Reference | None = None,
+                t_amp=0.01, v_ms=10.0):
+    """Bates + hydrostatic shell state, T x (1 + t_amp f), v = v_ms/a0 f_vec (f from the seeded
+    Fourier construction in Cartesian coordinates divided by the outer radius)."""
+    ref = ref or shell_reference()
+    xs = np.moveaxis(x, 1, -1)
+    r_nd = np.sqrt((xs ** 2).sum(-1))
+    rho_d, T_d = bates_hydrostatic(r_nd * ref.H0, ref)
+    unit = xs / desc.r_outer
+    fT = fourier_field(seed, 0, unit)
+    fv = [fourier_field(seed, s, unit) for s in (1, 2, 3)]
+    T = T_d / ref.T0 * (1.0 + t_amp * fT)
+    v = np.stack([v_ms / ref.a0 * f for f in fv])
+    rho = rho_d / ref.rho0
+    v = np.moveaxis(v, 0, 0)
+    return pack_state(rho, v, T)
+
+
+def isothermal_column(x: np.ndarray, T=1.0, g=1.0):
+    """Hydrostatic isothermal column under constant gravity -g e_z: log rho = -g z / T, v = 0."""
+    z = x[:, 2, :]
+    rho = np.exp(-g * z / T)
+    zeros = np.zeros_like(z)
+    return pack_state(rho, np.stack([zeros, zeros, zeros]), T * np.ones_like(z))
+
+
+def state_for(desc: MeshDesc, x: np.ndarray, seed: int):
+    if desc.kind == KIND_BOX:
+        return box_state(x, seed)
+    return shell_state(x, desc, seed)

@@ -1,0 +1,282 @@
+"""Pins of the oracle's LDG gradient, residual and Jv (Eq. DGformulation, Eq. LDG2)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dg as D
+from oracle import mesh as OM
+from oracle import physics as P
+from paper_2306_01085_gb300 import workloads as W
+
+TWO_PI = 2 * math.pi
+
+
+def periodic_fields(x):
+    X, Y, Z = x
+    rho = np.exp(0.2 * np.sin(TWO_PI * (X + Y)) + 0.1 * np.cos(TWO_PI * Z))
+    v = np.stack([0.1 * np.sin(TWO_PI * (X + Z)), 0.1 * np.cos(TWO_PI * (Y - X)),
+                  0.1 * np.sin(TWO_PI * (X + Y + Z))])
+    T = 1.0 + 0.2 * np.cos(TWO_PI * (X - Z)) + 0.1 * np.sin(TWO_PI * Y)
+    return rho, v, T
+
+
+def u_of(x):
+    rho, v, T = periodic_fields(x)
+    s = np.sqrt(rho)
+    return np.stack([np.log(rho), s * v[0], s * v[1], s * v[2], s * T])
+
+
+def nodal(mesh, fun):
+    return np.moveaxis(fun(np.moveaxis(mesh.X, 1, 0)), 0, 1)       # [e, c, i]
+
+
+def test_free_stream_is_preserved():
+    d = W.box_desc(p=2, n=3)
+    d.gvec = (0.0, 0.0, 0.0)
+    m = OM.OracleMesh(d)
+    u0 = np.array([-0.3, 0.2 * math.exp(-0.15), -0.1 * math.exp(-0.15), 0.05 * math.exp(-0.15),
+                   1.2 * math.exp(-0.15)])
+    u = np.broadcast_to(u0[None, :, None], (m.n_elem, 5, m.Np)).copy()
+    q = D.gradient(m, u)
+    assert np.abs(q).max() < 1e-12
+    r = D.residual(m, u)
+    assert np.abs(r).max() < 1e-13
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_gradient_exact_for_polynomials(p):
+    d = W.box_desc(p=p, n=2, bc_lo=W.BC_OUTFLOW, bc_hi=W.BC_OUTFLOW)
+    m = OM.OracleMesh(d)
+    z = m.X[:, 2, :]
+    coef = np.array([[0.3, -1.0, 0.5, 0.25][: p + 1]])
+    u = np.stack([sum(c * z ** k for k, c in enumerate(np.roll(coef[0], s))) for s in range(5)], axis=1)
+    du = np.stack([sum(k * c * z ** (k - 1) for k, c in enumerate(np.roll(coef[0], s)) if k > 0) + 0 * z
+                   for s in range(5)], axis=1)
+    q = D.gradient(m, u)
+    assert np.abs(q[:, 0]).max() < 1e-12 and np.abs(q[:, 1]).max() < 1e-12
+    assert np.abs(q[:, 2] - du).max() < 1e-12
+
+
+def test_gradient_converges_on_periodic_box():
+    errs = []
+    for n in (2, 4, 8):
+        m = OM.OracleMesh(W.box_desc(p=2, n=n))
+        u = nodal(m, u_of)
+        q = D.gradient(m, u)
+        from tests.test_oracle_physics import cs_grad
+        qex = np.moveaxis(cs_grad(u_of, np.moveaxis(m.X, 1, 0).reshape(3, -1)).reshape(3, 5, m.n_elem, m.Np), 2, 0)
+        errs.append(np.abs(q - qex).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > 1.8, (errs, rates)
+
+
+@pytest.mark.parametrize("kind", ["box", "shell"])
+def test_discrete_conservation(kind):
+    """sum_i r_{c,i} over all nodes = int s_c - (boundary fluxes): partition of unity + single-valued
+    interior fluxes (the volume flux term vanishes for w = 1 and interior face terms cancel)."""
+    if kind == "box":
+        d = W.box_desc(p=2, n=3)
+        m = OM.OracleMesh(d)
+        u = W.box_state(m.X, seed=5, amp=0.05)
+    else:
+        d = W.shell_desc(n=2, nr=2, p=2, euv=True)
+        d.h_first = 0.0
+        m = OM.OracleMesh(d)
+        u = W.shell_state(m.X, d, seed=3)
+    C = P.Coeffs(d)
+    q = D.gradient(m, u)
+    r = D.residual(m, u, q, t=0.3)
+    uG = np.moveaxis(np.einsum("gi,eci->ecg", m.phi, u), 0, 1)
+    qG = np.moveaxis(np.einsum("gi,edci->edcg", m.phi, q), 0, 2)
+    s = P.source(uG, qG, np.moveaxis(m.xG, 1, 0), 0.3, C)
+    Wd = m.W[None, :] * m.detJ
+    int_s = np.einsum("eg,ceg->c", Wd, s)
+    fh = D.face_fluxes(m, u, q, np.arange(m.n_elem), C)
+    bnd = np.einsum("x,efcx->efc", m.wF, fh)
+    bmask = (m.nbr_elem < 0)[:, :, None]
+    total = int_s - (bnd * bmask).sum((0, 1))
+    scale = np.abs(r).sum((0, 2))
+    assert np.all(np.abs(r.sum((0, 2)) - total) < 1e-12 * scale), (r.sum((0, 2)), total)
+
+
+def test_translation_equivariance():
+    d = W.box_desc(p=2, n=3)
+    m = OM.OracleMesh(d)
+    u = W.box_state(m.X, seed=11, amp=0.05)
+    n = d.nx
+    e = np.arange(m.n_elem).reshape(n, n, n)          # [k, j, i]
+    shifted = np.roll(e, -1, axis=2).ravel()          # element (i, j, k) takes (i+1, j, k)
+    r = D.residual(m, u)
+    r_s = D.residual(m, u[shifted])
+    assert np.abs(r_s - r[shifted]).max() < 1e-13 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("re,min_rate", [(1e8, 1.7), (20.0, 0.9)])
+def test_consistency_with_strong_form(re, min_rate):
+    """M^{-1} r(I_h u) -> -div F(u, grad u) + s(u, grad u) at the nodes (p = 2).
+
+    Interpolated smooth data: rate p for the inviscid part; with viscosity the LDG second-derivative
+    consistency error of interpolated data is O(h^{p-1}) (q is the gradient of the interpolant and
+    is discontinuous across faces), so the viscous case is held to p - 1.
+    """
+    from tests.test_oracle_physics import fd_div, cs_grad
+    errs = []
+    for n in (2, 4, 8):
+        d = W.box_desc(p=2, n=n, re=re, visc_exp=0.69)
+        m = OM.OracleMesh(d)
+        C = P.Coeffs(d)
+        u = nodal(m, u_of)
+        r = D.residual(m, u, t=0.0)
+        Mmat = np.einsum("eg,gi,gj->eij", m.W[None, :] * m.detJ, m.phi, m.phi)
+        dudt = np.linalg.solve(Mmat, r.transpose(0, 2, 1)).transpose(0, 2, 1)
+        xs = np.moveaxis(m.X, 1, 0).reshape(3, -1)
+        flux_x = lambda y: P.flux(u_of(y), cs_grad(u_of, y), C)
+        strong = -fd_div(flux_x, xs, h=1e-4) + P.source(u_of(xs), cs_grad(u_of, xs), xs, 0.0, C)
+        strong = np.moveaxis(strong.reshape(5, m.n_elem, m.Np), 0, 1)
+        errs.append(np.sqrt(np.mean((dudt - strong) ** 2)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > min_rate, (errs, rates)
+
+
+def test_hydrostatic_balance_converges():
+    """Isothermal column under constant gravity, wall bottom / outflow top: M^{-1} r -> 0 at rate p
+    (near-inviscid, Re = 1e8; the exponential is interpolated, so balance is not exact)."""
+    errs = []
+    for nz in (2, 4, 8):
+        d = W.box_desc(p=2, n=1, nz=nz, bc_lo=W.BC_WALL, bc_hi=W.BC_OUTFLOW, re=1e8)
+        m = OM.OracleMesh(d)
+        u = W.isothermal_column(m.X, T=1.0, g=1.0)
+        r = D.residual(m, u)
+        Mmat = np.einsum("eg,gi,gj->eij", m.W[None, :] * m.detJ, m.phi, m.phi)
+        dudt = np.linalg.solve(Mmat, r.transpose(0, 2, 1)).transpose(0, 2, 1)
+        errs.append(np.abs(dudt).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 2e-4 and rates[-1] > 1.8, (errs, rates)
+
+
+@pytest.mark.parametrize("kind", ["box", "shell"])
+def test_jvp_matches_central_differences(kind):
+    if kind == "box":
+        d = W.box_desc(p=1, n=2, bc_lo=W.BC_WALL, bc_hi=W.BC_OUTFLOW, visc_exp=0.69)
+        m = OM.OracleMesh(d)
+        u = W.box_state(m.X, seed=3, amp=0.05)
+    else:
+        d = W.shell_desc(n=1, nr=4, p=2, euv=True)
+        d.h_first = 0.0
+        d.grashof = 50.0 ** 2 / d.gamma
+        m = OM.OracleMesh(d)
+        u = W.shell_state(m.X, d, seed=4)
+    v = W.unit_vector(9, u.shape)
+    jv = D.jvp(m, u, v, t=0.2)
+    h = 1e-6
+    fd = (D.residual(m, u + h * v, t=0.2) - D.residual(m, u - h * v, t=0.2)) / (2 * h)
+    for c in range(5):
+        assert np.abs(jv[:, c] - fd[:, c]).max() < 1e-6 * np.abs(jv[:, c]).max() + 1e-12
+
+
+def test_full_fd_jacobian_on_tiny_mesh():
+    """Brute force: every column of J by central differences, then J v against the complex step."""
+    d = W.box_desc(p=1, n=1, nz=2, bc_lo=W.BC_WALL, bc_hi=W.BC_OUTFLOW, visc_exp=0.69)
+    m = OM.OracleMesh(d)
+    u = W.box_state(m.X, seed=8, amp=0.05)
+    n = u.size
+    h = 1e-6
+    J = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = h
+        J[:, j] = ((D.residual(m, u + e.reshape(u.shape)) - D.residual(m, u - e.reshape(u.shape))) / (2 * h)).ravel()
+    v = W.unit_vector(2, u.shape)
+    jv = D.jvp(m, u, v).ravel()
+    assert np.abs(J @ v.ravel() - jv).max() < 1e-7 * np.abs(jv).max()
+
+
+def test_piecewise_constant_state_closed_forms():
+    """Per-element constant varrho with v = 0 on the periodic box (affine, exact quadrature):
+    (1) LDG lifting: int_K q_d = sum_faces (u_nb - u_K)/2 * (n_d |face|), since u_hat is the average;
+    (2) varrho equation: F = 0 and s = 0 inside, so sum_i r = -sum_faces lambda/2 (rho_K - rho_nb) |face|
+        (the global Lax-Friedrichs term sigma_c (u - u_hat) of Eq. LDG2)."""
+    n = 3
+    d = W.box_desc(p=2, n=n)
+    d.lambda0 = 1.7
+    m = OM.OracleMesh(d)
+    rng = np.random.default_rng(4)
+    rho_e = rng.uniform(-0.5, 0.5, m.n_elem)
+    u = np.zeros((m.n_elem, 5, m.Np))
+    u[:, 0] = rho_e[:, None]
+    u[:, 4] = np.exp(0.5 * rho_e)[:, None]
+    q = D.gradient(m, u)
+    Wd = m.W[None, :] * m.detJ
+    qG = np.einsum("gi,edci->edcg", m.phi, q)
+    int_q = np.einsum("eg,edcg->edc", Wd, qG)
+    area = (1.0 / n) ** 2
+    normals = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, 0], [0, 1, 0], [0, 0, -1], [0, 0, 1]], float)
+    expect_q = np.zeros((m.n_elem, 3, 5))
+    expect_r = np.zeros(m.n_elem)
+    for e in range(m.n_elem):
+        for f in range(6):
+            nb = m.nbr_elem[e, f]
+            jump = u[nb, :, 0] - u[e, :, 0]
+            expect_q[e] += 0.5 * area * normals[f][:, None] * jump[None, :]
+            expect_r[e] += -0.5 * d.lambda0 * (rho_e[e] - rho_e[nb]) * area
+    assert np.abs(int_q - expect_q).max() < 1e-13
+    r = D.residual(m, u, q)
+    assert np.abs(r[:, 0].sum(1) - expect_r).max() < 1e-13
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_gradient_of_linear_field_on_curved_shell(p):
+    """u = a . x lies in the isoparametric space; q equals a up to the quadrature error of the
+    curved elements, which shrinks as p grows."""
+    errs = []
+    for pp in (p, p + 1):
+        d = W.shell_desc(n=2, nr=2, p=pp)
+        d.h_first = 0.0
+        d.bc_lo = d.bc_hi = W.BC_OUTFLOW
+        m = OM.OracleMesh(d)
+        a = np.array([0.3, -0.7, 0.45])
+        lin = np.einsum("d,edi->ei", a, m.X)
+        u = np.stack([lin, 2 * lin, -lin, 0.5 * lin, 3 * lin], axis=1)
+        q = D.gradient(m, u)
+        expect = a[None, :, None, None] * np.array([1, 2, -1, 0.5, 3])[None, None, :, None]
+        errs.append(np.abs(q - expect).max() / np.abs(expect).max())
+    assert errs[0] < 5e-2 and errs[1] < 0.5 * errs[0]
+
+
+def test_wall_mass_flux_vanishes():
+    """No-slip wall: the varrho flux through the wall is exactly zero (v_hat = 0, varrho_hat = varrho)."""
+    d = W.shell_desc(n=2, nr=3, p=2)
+    d.h_first = 0.0
+    m = OM.OracleMesh(d)
+    u = W.shell_state(m.X, d, seed=6, v_ms=200.0)
+    u[:, 0] += 0.4                                  # varrho = 0 at the lower boundary otherwise
+    C = P.Coeffs(d)
+    q = D.gradient(m, u)
+    fh = D.face_fluxes(m, u, q, np.arange(m.n_elem), C)
+    wall = m.bc == 1
+    out = m.bc == 2
+    assert np.abs(fh[wall][:, 0]).max() < 1e-14 * np.abs(fh[out][:, 0]).max() + 1e-300
+    assert np.abs(fh[out][:, 0]).max() > 0
+
+
+def test_free_stream_on_curved_shell():
+    """Uniform state without gravity or rotation, outflow on both spheres. The volume flux term
+    integrates d phi/d xi_e times cofactor entries of degree 3p-1 per direction: exact with the
+    (p+1)-point Gauss rule for p <= 2 (free stream preserved to rounding), otherwise r != 0 but it
+    must vanish spectrally as p grows."""
+    res = []
+    for p in (2, 3, 4, 5):
+        d = W.shell_desc(n=2, nr=3, p=p, rotation=False)
+        d.h_first = 0.0
+        d.g_r0 = 0.0
+        d.bc_lo = d.bc_hi = W.BC_OUTFLOW
+        m = OM.OracleMesh(d)
+        u0 = np.array([0.2, 0.33, -0.22, 0.11, 1.21])
+        u = np.broadcast_to(u0[None, :, None], (m.n_elem, 5, m.Np)).copy()
+        r = D.residual(m, u)
+        interior = np.all(m.nbr_elem >= 0, axis=1)
+        area = (m.W[None, :] * m.detJ).sum(1)[interior].min() ** (2 / 3)
+        res.append(np.abs(r[interior]).max() / area)
+    assert res[0] < 1e-13, res
+    assert res[1] < 1e-5 and res[2] < 0.3 * res[1] and res[3] < 0.3 * res[2], res
