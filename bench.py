@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput of the DG residual + exact Jacobian-vector product (DOFs/s) on one GB300.
+
+Workload (default): cubed-sphere shell 6 x 16 x 16 surface cells x 8 radial layers (12,288 hexes),
+p = 4 (125 GLL nodes per element, 7,680,000 unknowns), Bates + hydrostatic base state with 1 % T
+and 10 m/s seeded perturbations, rotation, radial gravity, mu ~ T^0.69, wall bottom / outflow top.
+One step = one fused evaluation of r(u) and J(u) v (dg_jvp, exact mode) in FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank evaluates its own replica of the workload (independent problems, no
+collective on the data path); `value` = all ranks' unknowns / max over ranks of the step time.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DG residual+Jv DOFs/s"
+UNIT = "DOF/s"
+CONFIG_NAME = "shell16x8_p4"
+FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64 (profiling recipe nominal table)
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default=CONFIG_NAME)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------------
+# oracle timing (cpu_baseline leg and --impl reference): the oracle as it stands, one thread
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(desc, block):
+    """A contiguous block of elements (panel 0, block x block cells, all layers) of the shell, or
+    the first block^2 * nz elements of a box."""
+    import numpy as np
+    if desc.kind == 1:
+        nz, n = desc.nz, desc.nx
+        return np.array([k + nz * (i + n * j) for j in range(block) for i in range(block) for k in range(nz)])
+    return np.arange(min(desc.n_elem, block * block * desc.nz))
+
+
+def cpu_worker(config, steps, block):
+    """Time the oracle's residual + Jv on a sample of elements; prints JSON (runs in a child)."""
+    import numpy as np
+    from oracle import dg as OD
+    from oracle import mesh as OM
+    from paper_2306_01085_gb300 import workloads as W
+    desc = W.CONFIGS[config][0]()
+    om = OM.OracleMesh(desc)
+    u = W.state_for(desc, om.X, 2)
+    v = W.unit_vector(102, u.shape)
+    sample = oracle_sample(desc, block)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        OD.residual(om, u, None, 0.0, elems=sample)
+        OD.jvp(om, u, v, 0.0, elems=sample)
+        times.append(time.perf_counter() - t0)
+    dof = len(sample) * 5 * om.Np
+    print(json.dumps({"times": times, "dof": dof, "elements": int(len(sample))}))
+
+
+def run_cpu_worker(config, steps, block):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", str(block), "--config", config,
+           "--steps", str(steps)]
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------------
+# algorithmic FP64 work of the kernels (per element, per launch), see the design doc
+# ----------------------------------------------------------------------------------------------
+def fp64_flops_per_element(kernel, n, tangent=True):
+    """FP64 flops per element of one kernel launch counted from the algorithm (FMA = 2 flops).
+
+    Contractions are counted exactly; the pointwise flux/source/EUV part uses the per-point FP64
+    operation counts stated in the design doc (value + tangent with dual numbers)."""
+    NP, NF = n ** 3, n * n
+    C = 10 if tangent else 5
+    if kernel == "k_volume":
+        proj = 3 * C * 3 * 2                       # Fref_a = sum_d G_ad F_cd (value + tangent)
+        weak = 3 * C * n * 2                       # sum_a D_a^T Fref_a
+        lift = 6 * C * 2
+        bt = 3 * C * n * 2                         # B^T along three directions
+        point = 560 if tangent else 250            # pointwise flux + source per Gauss point
+        return NP * (proj + weak + lift + bt + point)
+    if kernel == "k_grad":
+        return NP * C * (9 + 3 * 3 * n * 2 + 6 * 3 * 2 + 3) + 6 * NF * C
+    if kernel == "k_faces":
+        return 3 * NF * (2 * (520 if tangent else 230) + 120)
+    if kernel == "k_interp":
+        return NP * C * 3 * n * 2 + 6 * NF * C * n * 2
+    return 0
+
+
+def main_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2306_01085_gb300 import build as B
+    from paper_2306_01085_gb300 import dg as DG
+    from paper_2306_01085_gb300 import workloads as W
+
+    B.build()
+    desc = W.CONFIGS[args.config][0]()
+    mesh = DG.Mesh(desc)
+    x = mesh.nodes().cpu().numpy()
+    u = W.state_for(desc, x, 2 + rank)
+    v = W.unit_vector(102 + rank, u.shape)
+    ug = torch.from_numpy(u).cuda()
+    vg = torch.from_numpy(v).cuda()
+    r = torch.empty_like(ug)
+    jv = torch.empty_like(ug)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        mesh.jvp(ug, vg, t=0.0, out=jv, r_out=r)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if not (torch.isfinite(r).all() and torch.isfinite(jv).all()):
+        raise RuntimeError("non-finite residual or Jv")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mesh.profile_start(capacity=64 * args.steps + 64)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                 # write 2x L2 between steps (outside the events)
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    prof, launches = mesh.profile_stop()
+    clk = clocks.stop()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_mean = sum(ms) / len(ms)
+    t = torch.tensor([ms_mean], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * mesh.n_dof / (ms_max * 1e-3)
+
+    # dominant kernel and its FP64 roofline
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_cnt) = dom
+    per_launch_ms = dom_ms / dom_cnt
+    flops = fp64_flops_per_element(dom_name, desc.p + 1) * mesh.n_elem
+    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+    probe = DG.probe_fp64()
+    roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4), "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                "peak_kind": "FP64 nominal of the profiling recipe", "peak_probe": round(probe, 4),
+                "launch_ms": round(per_launch_ms, 4), "fp64_flops_per_launch": flops,
+                "share": round(dom_ms / sum(v[0] for v in prof.values()), 4)}
+
+    # end to end through the public API: pinned host in, host out, every step
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.from_numpy(u).pin_memory()
+        vh = torch.from_numpy(v).pin_memory()
+        rh = torch.empty_like(uh).pin_memory()
+        jh = torch.empty_like(uh).pin_memory()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        for k in range(args.warmup + args.steps):
+            if k == args.warmup:
+                torch.cuda.synchronize()
+                ev0.record(stream)
+            ug.copy_(uh, non_blocking=True)
+            vg.copy_(vh, non_blocking=True)
+            step()
+            rh.copy_(r, non_blocking=True)
+            jh.copy_(jv, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = ev0.elapsed_time(ev1) / args.steps
+        te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * mesh.n_dof / (float(te.item()) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 8 * mesh.n_dof, "d2h_bytes_per_step": 2 * 8 * mesh.n_dof}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = run_cpu_worker(args.config, 1, 4)
+        cpu = {"value": res["dof"] / min(res["times"]), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"residual + complex-step Jv of {res['elements']} contiguous elements "
+                         f"({res['dof']} DOF; panel 0, 4x4 cells, all layers) of the same shell, one thread"}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": f"{args.config}: {W.CONFIGS[args.config][1]}", "n_elem": mesh.n_elem,
+                          "p": desc.p, "n_dof": mesh.n_dof, "step": "fused residual + exact Jv (dg_jvp)",
+                          "l2": "2x L2 buffer written between timed steps", "parallelism": f"replicas x{world}"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+               "kernels": {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items()},
+               "clocks": clk, "wall_s_timed": round(wall, 4)}
+        print(json.dumps(out), flush=True)
+    mesh.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_reference(args):
+    """The oracle (this repository's CPU reference of the method) on the same workload, one thread."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sys.path.insert(0, ROOT)
+    from paper_2306_01085_gb300 import workloads as W
+    res = run_cpu_worker(args.config, args.warmup + args.steps, 2)
+    times = res["times"][args.warmup:] or res["times"]
+    ms = 1e3 * sum(times) / len(times)
+    value = res["dof"] / (ms * 1e-3)
+    sample = (f"residual + complex-step Jv of {res['elements']} contiguous elements ({res['dof']} DOF) of the "
+              f"same shell per step, one thread")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.config}: {W.CONFIGS[args.config][1]}"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.cpu_worker:
+        cpu_worker(a.config, a.steps, a.cpu_worker)
+    elif a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

@@ -1,0 +1,156 @@
+/*
+ * dg.h - C ABI of the GB300 library for the high-order LDG discretisation of the thermosphere
+ * model of Vila-Perez, Nguyen & Peraire (arXiv 2306.01085).
+ *
+ * The operations follow the semi-discrete form of Sec. 3.1 (Eq. DGformulation with the LDG trace
+ * and flux of Eq. LDG2) for the nondimensional system of Eq. fluxSWNondimensional, and the
+ * matrix-free Newton-GMRES solution of the DIRK stages of Sec. 3.1-3.2.
+ *
+ * Conventions (all calls):
+ *   - Every pointer named u, q, r, v, jv, x, y is a DEVICE pointer owned by the caller, on the
+ *     device that was current when the mesh was created. The library never frees them.
+ *   - Layouts (row-major, contiguous, FP64 unless stated):
+ *       u, r, v, jv  [n_elem][5][n_p]        variables (varrho, sqrt(rho) v_x, v_y, v_z, sqrt(rho) T)
+ *       q            [n_elem][3][5][n_p]     q[e][d][c][i] ~ d u_c / d x_d (LDG gradient)
+ *       x            [n_elem][3][n_p]        node coordinates (nondimensional)
+ *     n_p = (p+1)^3 nodes per element: tensor GLL nodes, node i = a + (p+1) b + (p+1)^2 c with a
+ *     along the first reference coordinate. Values are nodal coefficients of the Lagrange basis.
+ *   - Element numbering: box e = i + nx (j + ny k); shell e = k + nz (i + nx (j + nx P)) for panel
+ *     P (cube faces centred on +x, +y, -x, -y, +z, -z), angular cell (i, j) and radial layer k.
+ *   - stream is a cudaStream_t (NULL: the legacy default stream). Calls are stream-ordered and
+ *     asynchronous unless stated; the host reads back only what a call documents.
+ *   - Every call returns DG_OK (0) or a negative status; dg_last_error() gives a thread-local
+ *     message. No exception crosses the ABI.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK        0
+#define DG_EINVAL   -1   /* bad argument (null pointer, unsupported size, p out of range) */
+#define DG_ECUDA    -2   /* a CUDA call failed; the message names it */
+#define DG_ENOMEM   -3   /* device allocation failed */
+#define DG_ENOTCONV -4   /* Newton or GMRES did not reach its tolerance within its limits */
+#define DG_ENAN     -5   /* a NaN or Inf appeared in a norm the solver checks */
+
+#define DG_KIND_BOX    0 /* [0,lx]x[0,ly]x[0,lz], periodic in x and y */
+#define DG_KIND_SHELL  1 /* cubed-sphere shell between r_inner and r_outer */
+
+#define DG_BC_PERIODIC 0 /* box z ends only: periodic in z */
+#define DG_BC_WALL     1 /* no-slip isothermal wall (Sec. 2.5): u_hat = (varrho,0,0,0,e^{varrho/2} T_wall) */
+#define DG_BC_OUTFLOW  2 /* adiabatic, zero viscous normal stress: u_hat = u, F_hat.n = F_inv(u).n */
+
+#define DG_JV_EXACT 0    /* exact directional derivative (forward-mode tangent of every step) */
+#define DG_JV_FD    1    /* one-sided difference (r(u + eps v) - r(u)) / eps (Sec. 3.2) */
+
+/* Problem description. Physics fields are the nondimensional numbers of Sec. 2.4. */
+typedef struct dg_mesh_desc {
+    int32_t kind;          /* DG_KIND_* */
+    int32_t p;             /* polynomial degree k, 1 <= p <= 4 */
+    int32_t nx, ny, nz;    /* box: elements per direction; shell: nx = panel cells per side, nz = layers */
+    int32_t bc_lo, bc_hi;  /* DG_BC_* of the lower (z = 0 / inner) and upper (z = lz / outer) boundary */
+    double lx, ly, lz;     /* box lengths */
+    double r_inner, r_outer, h_first; /* shell radii, first-layer height (<= 0: uniform layers) */
+    double gamma;          /* ratio of specific heats */
+    double grashof;        /* Gr; viscous coefficient 1/sqrt(gamma Gr) */
+    double prandtl;        /* Pr; conduction coefficient sqrt(gamma/Gr)/Pr */
+    double mass;           /* m* (c_v* = 1/m*) */
+    double visc_exp;       /* mu* = kappa* = T*^visc_exp (0: constant) */
+    double lambda0;        /* sigma_c = lambda0 I (global Lax-Friedrichs, Eq. LDG2) */
+    double t_wall;         /* wall temperature T* */
+    int32_t gravity_kind;  /* 0: constant g* = gvec; 1: g* = -(g_r0/|r|)^2 r/|r| */
+    int32_t euv;           /* 1: Gaussian sub-solar heating source */
+    double gvec[3];
+    double g_r0;
+    double omega[3];       /* rotation vector omega* */
+    double froude;         /* Fr */
+    double euv_amp;        /* peak heating Q* (nondimensional) */
+    double euv_sigma;      /* zenith-angle standard deviation [rad] */
+    double euv_r_peak;     /* radius of the peak */
+    double euv_width;      /* vertical half width at half maximum */
+    double euv_omega_t;    /* sub-solar rotation angle per unit nondimensional time */
+} dg_mesh_desc;
+
+typedef struct dg_mesh dg_mesh;
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* dg_last_error(void);
+
+/*
+ * Build the mesh (Sec. 3.3 cubed sphere with geometric radial growth, or a box), its face
+ * connectivity, and the isoparametric geometry at the quadrature points (Sec. 3.1: k-th degree
+ * curved elements; (p+1)^3 Gauss points per element, (p+1)^2 per face). Allocates all library
+ * storage on the current device and synchronises it. *out receives an opaque handle to release
+ * with dg_mesh_destroy. Errors: DG_EINVAL (p outside 1..4, non-positive sizes, inconsistent
+ * boundaries), DG_ENOMEM, DG_ECUDA.
+ */
+int dg_mesh_create(const dg_mesh_desc* desc, dg_mesh** out);
+
+/* Release every library allocation of the mesh (synchronises the device). NULL is ignored. */
+void dg_mesh_destroy(dg_mesh* mesh);
+
+/* Sizes: elements, nodes per element, unknowns (5 n_elem n_p). Any output pointer may be NULL. */
+int dg_mesh_sizes(const dg_mesh* mesh, int64_t* n_elem, int32_t* n_p, int64_t* n_dof);
+
+/* Copy the node coordinates x [n_elem][3][n_p] into a caller device buffer (stream-ordered). */
+int dg_mesh_nodes(const dg_mesh* mesh, double* x, void* stream);
+
+/*
+ * LDG gradient, Eq. DGformulation (first equation): q solves (q, p) = -(u, div p) + <u_hat, p.n>
+ * for every p in Q_h, with u_hat = (u + u^-)/2 on interior faces and the boundary traces of
+ * DG_BC_*. Output q is nodal, layout [n_elem][3][5][n_p]. u and q must not overlap.
+ */
+int dg_gradient(dg_mesh* mesh, const double* u, double* q, void* stream);
+
+/*
+ * Residual, Eq. DGformulation (second equation), tested against every nodal basis function:
+ *   r = (F(u,q), grad w) - <F_hat.n, w> + (s(u,q), w),   F_hat.n of Eq. LDG2,
+ * i.e. r = M du/dt. q: nodal gradient from dg_gradient, or NULL to compute it internally from u.
+ * t is the nondimensional time (used by the heating source). r must not overlap u or q.
+ */
+int dg_residual(dg_mesh* mesh, const double* u, const double* q, double t, double* r, void* stream);
+
+/*
+ * Jacobian-vector product of the residual, J v = d r(u + s v)/ds at s = 0 (Sec. 3.2), where q is
+ * recomputed from u (the LDG gradient is part of r).
+ *   mode DG_JV_EXACT: forward-mode tangent of every step; r_out (may be NULL) receives r(u) from
+ *                     the same pass.
+ *   mode DG_JV_FD:    (r(u + eps v) - r(u)) / eps. eps <= 0 selects
+ *                     eps = sqrt(2^-52) (1 + ||u||_2) / ||v||_2 (Knoll & Keyes 2004), which reads
+ *                     two norms back to the host (synchronises the stream). r_out may be NULL.
+ * jv must not overlap u, v or r_out.
+ */
+int dg_jvp(dg_mesh* mesh, const double* u, const double* v, double t, int32_t mode, double eps,
+           double* jv, double* r_out, void* stream);
+
+/* Mass matrix product (M v)_i = sum_j (phi_i, phi_j) v_j per element and variable (Sec. 3.1). */
+int dg_mass_apply(dg_mesh* mesh, const double* v, double* mv, void* stream);
+
+/*
+ * Tracing. dg_profile_start makes every kernel the library launches for this mesh record a pair
+ * of CUDA events on the stream it runs on (capacity = most launches recorded; launches beyond it
+ * are counted, not timed). dg_profile_stop synchronises those events, accumulates the device time
+ * per kernel kind into ms[kind] and the launches into count[kind] for kind < n_kinds (either
+ * array may be NULL), returns the total number of launches through *total (may be NULL), and
+ * switches tracing off. dg_kernel_name(kind) names a kind ("" past the last one).
+ */
+int dg_profile_start(dg_mesh* mesh, int32_t capacity);
+int dg_profile_stop(dg_mesh* mesh, int32_t n_kinds, double* ms, int32_t* count, int64_t* total);
+const char* dg_kernel_name(int32_t kind);
+
+/*
+ * FP64 throughput probe (the ceiling of the FP64 path, which is FP64-pipe bound on this part):
+ * a fused multiply-add loop over 8 independent chains per thread on every SM, timed with CUDA
+ * events on the legacy stream; *tflops receives the achieved FP64 TFLOP/s (2 flops per FMA).
+ */
+int dg_probe_fp64(double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

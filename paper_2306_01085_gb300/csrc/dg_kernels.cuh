@@ -1,0 +1,856 @@
+// FP64 element and face kernels of the LDG residual, its exact tangent and the mass matrix.
+//
+// Representation. A degree-p field on an element is held by its values at the (p+1)^3 Gauss
+// points ("Gauss space"). The ABI's nodal GLL coefficients map to Gauss space by B x B x B, with
+// B[q][a] = l^GLL_a(eta_q) invertible. In Gauss space the operators of Eq. DGformulation reduce
+// to exact sum-factorised 1D passes:
+//   derivative along xi_a ............ D (Lagrange derivative on the Gauss points)
+//   value on face xi_a = -1 / +1 ...... eL / eR (Lagrange extrapolation to the end points)
+//   test-function weak derivative .... D^T;  face lifting ... eL / eR outer products
+// and the element mass matrix is M = B^T W B with W = diag(w_g |J_g|), so
+//   Gradient (Eq. DGformulation a):  Q_{d,c} = W^{-1} [ -sum_a D_a^T (G_{a d} U_c)
+//                                                       + sum_faces e_face (w n_d dS) U_hat_c ]
+//   Residual (Eq. DGformulation b):  r = B^T [ sum_a D_a^T (sum_d G_{a d} F_{c d}) + W s_c
+//                                              - sum_faces e_face (F_hat . w n dS)_c ]
+// with G_{a d} = w_g |J| d xi_a / d x_d (cofactor of the Jacobian). Each identity is exact
+// (p-degree polynomials, the same quadrature), so these kernels compute the same discrete
+// operator as a dense nodal implementation, up to rounding.
+//
+// Kernels (one CTA handles EPB elements, one thread per Gauss point; faces one thread per point):
+//   k_interp   nodal u (and tangent v) -> Gauss values U, face traces UF
+//   k_grad     U, UF (own + neighbour) -> Q in Gauss space, face traces QF
+//   k_faces    UF, QF of both sides -> F_hat . (w n dS) for both element faces (Eq. LDG2)
+//   k_volume   U, Q, F_hat -> pointwise F, s; projection; lifting; B^T -> nodal r (and J v)
+// The exact Jacobian-vector product carries forward-mode dual numbers through every step.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <type_traits>
+
+#include "dg_internal.cuh"
+
+namespace dg {
+
+template <int N>
+struct Shape {
+  static constexpr int NP = N * N * N;
+  static constexpr int NF = N * N;
+};
+
+// elements per CTA by kernel footprint
+template <int N, int NC>
+struct Epb {
+  static constexpr int value = (N == 2) ? 16 : (N == 3) ? 8 : (N == 4) ? (NC == 1 ? 4 : 2) : (NC == 1 ? 2 : 1);
+};
+
+template <int N>
+__device__ __forceinline__ int pt_stride(int dir) {
+  return dir == 0 ? 1 : (dir == 1 ? N : N * N);
+}
+
+// 1D pass along `dir` at point g: sum_k A[i][k] in[.. k ..] (T = false) or A[k][i] (T = true)
+template <int N, bool T>
+__device__ __forceinline__ double line(const double* __restrict__ A, const double* __restrict__ in,
+                                       int g, int dir) {
+  const int st = pt_stride<N>(dir);
+  const int i = (g / st) % N;
+  const int base = g - i * st;
+  double acc = (T ? A[i] : A[i * N]) * in[base];
+#pragma unroll
+  for (int k = 1; k < N; ++k) acc = fma(T ? A[k * N + i] : A[i * N + k], in[base + k * st], acc);
+  return acc;
+}
+
+// Gauss point index of (face phi, face point f, index k along the face normal)
+template <int N>
+__device__ __forceinline__ int face_vol_point(int phi, int f, int k) {
+  const int axis = phi >> 1;
+  const int is = f % N, it = f / N;
+  int i0, i1, i2;
+  if (axis == 0) { i0 = k; i1 = is; i2 = it; }
+  else if (axis == 1) { i0 = is; i1 = k; i2 = it; }
+  else { i0 = is; i1 = it; i2 = k; }
+  return i0 + N * (i1 + N * i2);
+}
+
+// face point of volume point g on a face of the given axis
+template <int N>
+__device__ __forceinline__ int vol_face_point(int g, int axis) {
+  const int i0 = g % N, i1 = (g / N) % N, i2 = g / (N * N);
+  if (axis == 0) return i1 + N * i2;
+  if (axis == 1) return i0 + N * i2;
+  return i0 + N * i1;
+}
+
+template <int N>
+__device__ __forceinline__ int axis_index(int g, int axis) {
+  return axis == 0 ? g % N : (axis == 1 ? (g / N) % N : g / (N * N));
+}
+
+struct SmemOps {
+  double B[MAXN * MAXN], D[MAXN * MAXN], Binv[MAXN * MAXN], eL[MAXN], eR[MAXN];
+};
+
+template <int N>
+__device__ __forceinline__ void load_ops(const Ops* __restrict__ o, SmemOps& s) {
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    s.B[i] = o->B[i];
+    s.D[i] = o->D[i];
+    s.Binv[i] = o->Binv[i];
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    s.eL[i] = o->eL[i];
+    s.eR[i] = o->eR[i];
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// k_interp: nodal -> Gauss values and face traces. NC = 1 (u) or 2 (u and tangent v).
+// --------------------------------------------------------------------------------------------
+template <int N, int NC>
+__global__ void k_interp(const double* __restrict__ u, const double* __restrict__ v, long long E,
+                         const Ops* __restrict__ ops, double* __restrict__ ug, double* __restrict__ uf) {
+  constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
+  __shared__ SmemOps so;
+  extern __shared__ double smem[];
+  double* b0 = smem;                       // [EPB][C][NP]
+  double* b1 = smem + EPB * C * NP;        // [EPB][C][NP]
+  load_ops<N>(ops, so);
+  const long long e0 = (long long)blockIdx.x * EPB;
+  for (int idx = threadIdx.x; idx < EPB * 5 * NP; idx += blockDim.x) {
+    const int el = idx / (5 * NP), rem = idx % (5 * NP);
+    const long long e = e0 + el;
+    if (e < E) {
+      b0[(el * C) * NP + rem] = u[e * 5 * NP + rem];
+      if (NC == 2) b0[(el * C + 5) * NP + rem] = v[e * 5 * NP + rem];
+    }
+  }
+  __syncthreads();
+  const int el = threadIdx.x / NP, g = threadIdx.x % NP;
+  const bool active = el < EPB;
+  double* in = b0;
+  double* out = b1;
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    if (active)
+      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, false>(so.B, in + (el * C + c) * NP, g, dir);
+    __syncthreads();
+    double* t = in;
+    in = out;
+    out = t;
+  }
+  // `in` holds Gauss values
+  const long long plane_g = E * 5 * NP;
+  for (int idx = threadIdx.x; idx < EPB * 5 * NP; idx += blockDim.x) {
+    const int l = idx / (5 * NP), rem = idx % (5 * NP);
+    const long long e = e0 + l;
+    if (e < E) {
+      ug[e * 5 * NP + rem] = in[(l * C) * NP + rem];
+      if (NC == 2) ug[plane_g + e * 5 * NP + rem] = in[(l * C + 5) * NP + rem];
+    }
+  }
+  const long long plane_f = E * 6 * 5 * NF;
+  for (int idx = threadIdx.x; idx < EPB * 6 * 5 * NF; idx += blockDim.x) {
+    const int l = idx / (30 * NF), rem = idx % (30 * NF);
+    const int phi = rem / (5 * NF), c = (rem / NF) % 5, f = rem % NF;
+    const long long e = e0 + l;
+    if (e >= E) continue;
+    const double* ev = (phi & 1) ? so.eR : so.eL;
+    for (int pl = 0; pl < NC; ++pl) {
+      const double* src = in + (l * C + 5 * pl + c) * NP;
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc = fma(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
+      uf[pl * plane_f + e * 30 * NF + rem] = acc;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// k_grad: LDG gradient in Gauss space (Eq. DGformulation a) and its face traces
+// --------------------------------------------------------------------------------------------
+template <int N, int NC>
+__global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const double* __restrict__ geo,
+                       const double* __restrict__ fgeo, const int* __restrict__ nbr,
+                       const int* __restrict__ nbr_fo, const double* __restrict__ ug,
+                       const double* __restrict__ uf, double* __restrict__ qg, double* __restrict__ qf) {
+  constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
+  __shared__ SmemOps so;
+  extern __shared__ double smem[];
+  double* sU = smem;                        // [EPB][C][NP]
+  double* sUh = sU + EPB * C * NP;          // [EPB][6][C][NF]   U_hat
+  double* sN = sUh + EPB * 6 * C * NF;      // [EPB][6][3][NF]   w n dS
+  double* sY = sN + EPB * 6 * 3 * NF;       // [EPB][9][NP]
+  double* sQ = sY + EPB * 9 * NP;           // [EPB][3][C][NP]
+  load_ops<N>(ops, so);
+  const long long e0 = (long long)blockIdx.x * EPB;
+  const long long plane_g = E * 5 * NP, plane_f = E * 30 * NF;
+  for (int idx = threadIdx.x; idx < EPB * 5 * NP; idx += blockDim.x) {
+    const int l = idx / (5 * NP), rem = idx % (5 * NP);
+    const long long e = e0 + l;
+    if (e < E)
+      for (int pl = 0; pl < NC; ++pl) sU[(l * C + 5 * pl) * NP + rem] = ug[pl * plane_g + e * 5 * NP + rem];
+  }
+  // traces: u_hat on every face point (Eq. LDG2), and the face geometry
+  for (int idx = threadIdx.x; idx < EPB * 6 * NF; idx += blockDim.x) {
+    const int l = idx / (6 * NF), phi = (idx / NF) % 6, f = idx % NF;
+    const long long e = e0 + l;
+    if (e >= E) continue;
+    const long long fbase = e * 30 * NF + phi * 5 * NF + f;
+    for (int d = 0; d < 3; ++d) sN[((l * 6 + phi) * 3 + d) * NF + f] = fgeo[((e * 6 + phi) * 4 + d) * NF + f];
+    const int nb = nbr[e * 6 + phi];
+    double own[10], oth[10];
+    for (int pl = 0; pl < NC; ++pl)
+      for (int c = 0; c < 5; ++c) own[5 * pl + c] = uf[pl * plane_f + fbase + c * NF];
+    double* dst = sUh + ((l * 6 + phi) * C) * NF + f;
+    if (nb >= 0) {
+      const int fo = nbr_fo[e * 6 + phi];
+      const int f2 = orient_map(fo >> 3, f % N, f / N, N);
+      const long long nbase = (long long)nb * 30 * NF + (fo & 7) * 5 * NF + f2;
+      for (int pl = 0; pl < NC; ++pl)
+        for (int c = 0; c < 5; ++c) oth[5 * pl + c] = uf[pl * plane_f + nbase + c * NF];
+      for (int c = 0; c < C; ++c) dst[c * NF] = 0.5 * (own[c] + oth[c]);
+    } else if (nb == -DG_BC_WALL) {
+      const double sr = exp(0.5 * own[0]);
+      dst[0] = own[0];
+      dst[NF] = 0.0;
+      dst[2 * NF] = 0.0;
+      dst[3 * NF] = 0.0;
+      dst[4 * NF] = sr * P.t_wall;
+      if (NC == 2) {
+        dst[5 * NF] = own[5];
+        dst[6 * NF] = 0.0;
+        dst[7 * NF] = 0.0;
+        dst[8 * NF] = 0.0;
+        dst[9 * NF] = 0.5 * sr * P.t_wall * own[5];
+      }
+    } else {
+      for (int c = 0; c < C; ++c) dst[c * NF] = own[c];
+    }
+  }
+  __syncthreads();
+  const int el = threadIdx.x / NP, g = threadIdx.x % NP;
+  const bool active = el < EPB && (e0 + el) < E;
+  double G[9], invW = 0.0;
+  if (active) {
+    const double* gp = geo + (e0 + el) * 10 * NP + g;
+    for (int k = 0; k < 9; ++k) G[k] = gp[k * NP];
+    invW = 1.0 / gp[9 * NP];
+  }
+  for (int c = 0; c < C; ++c) {
+    if (active) {
+      const double uc = sU[(el * C + c) * NP + g];
+      for (int k = 0; k < 9; ++k) sY[(el * 9 + k) * NP + g] = G[k] * uc;
+    }
+    __syncthreads();
+    if (active) {
+      // lifting of the traces: sum over the 6 faces of e_face[i_axis] (w n_d dS) u_hat_c
+      double lift[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int phi = 0; phi < 6; ++phi) {
+        const int axis = phi >> 1;
+        const double coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
+        const int f = vol_face_point<N>(g, axis);
+        const double uh = sUh[((el * 6 + phi) * C + c) * NF + f];
+        for (int d = 0; d < 3; ++d) lift[d] = fma(coef * sN[((el * 6 + phi) * 3 + d) * NF + f], uh, lift[d]);
+      }
+      for (int d = 0; d < 3; ++d) {
+        double acc = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc += line<N, true>(so.D, sY + (el * 9 + a * 3 + d) * NP, g, a);
+        sQ[((el * 3 + d) * C + c) * NP + g] = (lift[d] - acc) * invW;
+      }
+    }
+    __syncthreads();
+  }
+  // write Q (Gauss space) and its face traces
+  for (int idx = threadIdx.x; idx < EPB * 15 * NP; idx += blockDim.x) {
+    const int l = idx / (15 * NP), rem = idx % (15 * NP);
+    const int d = rem / (5 * NP), c = (rem / NP) % 5, gg = rem % NP;
+    const long long e = e0 + l;
+    if (e < E)
+      for (int pl = 0; pl < NC; ++pl)
+        qg[pl * E * 15 * NP + e * 15 * NP + rem] = sQ[((l * 3 + d) * C + 5 * pl + c) * NP + gg];
+  }
+  for (int idx = threadIdx.x; idx < EPB * 6 * 15 * NF; idx += blockDim.x) {
+    const int l = idx / (90 * NF), rem = idx % (90 * NF);
+    const int phi = rem / (15 * NF), dc = (rem / NF) % 15, f = rem % NF;
+    const int d = dc / 5, c = dc % 5;
+    const long long e = e0 + l;
+    if (e >= E) continue;
+    const double* ev = (phi & 1) ? so.eR : so.eL;
+    for (int pl = 0; pl < NC; ++pl) {
+      const double* src = sQ + ((l * 3 + d) * C + 5 * pl + c) * NP;
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc = fma(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
+      qf[pl * E * 90 * NF + e * 90 * NF + rem] = acc;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// k_faces: numerical flux of Eq. LDG2 on every face, written for both element faces
+// --------------------------------------------------------------------------------------------
+template <typename S, int NC>
+__device__ __forceinline__ S ld(const double* p, long long plane) {
+  if constexpr (NC == 1) return p[0];
+  else return Dual{p[0], p[plane]};
+}
+template <typename S>
+__device__ __forceinline__ void st(double* p, long long plane, S v);
+template <>
+__device__ __forceinline__ void st<double>(double* p, long long, double v) { p[0] = v; }
+template <>
+__device__ __forceinline__ void st<Dual>(double* p, long long plane, Dual v) {
+  p[0] = v.v;
+  p[plane] = v.d;
+}
+
+template <int N, int NC>
+__global__ void k_faces(long long E, long long F, Phys P, const int* __restrict__ face_e,
+                        const int* __restrict__ face_f, const int* __restrict__ nbr,
+                        const int* __restrict__ nbr_fo, const double* __restrict__ fgeo,
+                        const double* __restrict__ uf, const double* __restrict__ qf,
+                        double* __restrict__ fh) {
+  using S = typename std::conditional<NC == 2, Dual, double>::type;
+  constexpr int NF = Shape<N>::NF;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= F * NF) return;
+  const long long fi = idx / NF;
+  const int f = (int)(idx % NF);
+  const long long e = face_e[fi];
+  const int phi = face_f[fi];
+  const long long plane_u = E * 30 * NF, plane_q = E * 90 * NF;
+  const double* gp = fgeo + ((e * 6 + phi) * 4) * NF + f;
+  const double n[3] = {gp[0], gp[NF], gp[2 * NF]};
+  const double area = gp[3 * NF];
+  S u[5], q[3][5];
+  const long long ub = e * 30 * NF + phi * 5 * NF + f;
+  const long long qb = e * 90 * NF + phi * 15 * NF + f;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) u[c] = ld<S, NC>(uf + ub + c * NF, plane_u);
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) q[d][c] = ld<S, NC>(qf + qb + (d * 5 + c) * NF, plane_q);
+  const int nb = nbr[e * 6 + phi];
+  S out[5];
+  if (nb >= 0) {
+    const int fo = nbr_fo[e * 6 + phi];
+    const int phi2 = fo & 7;
+    const int f2 = orient_map(fo >> 3, f % N, f / N, N);
+    S u2[5], q2[3][5];
+    const long long ub2 = (long long)nb * 30 * NF + phi2 * 5 * NF + f2;
+    const long long qb2 = (long long)nb * 90 * NF + phi2 * 15 * NF + f2;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u2[c] = ld<S, NC>(uf + ub2 + c * NF, plane_u);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) q2[d][c] = ld<S, NC>(qf + qb2 + (d * 5 + c) * NF, plane_q);
+    S f1[5], fn[5], uh[5], sg[5];
+    flux_dot_n(P, u, q, n, true, f1);
+    flux_dot_n(P, u2, q2, n, true, fn);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) uh[c] = 0.5 * (u[c] + u2[c]);
+    sigma_diag(P, uh, sg);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c] = 0.5 * (f1[c] + fn[c]) + sg[c] * ((0.5 * area) * (u[c] - u2[c]));
+    const long long ob2 = (long long)nb * 30 * NF + phi2 * 5 * NF + f2;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) st<S>(fh + ob2 + c * NF, plane_u, -out[c]);
+  } else if (nb == -DG_BC_WALL) {
+    S ubd[5], sg[5];
+    wall_trace(P, u, ubd);
+    flux_dot_n(P, ubd, q, n, true, out);
+    sigma_diag(P, ubd, sg);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c] = out[c] + sg[c] * (area * (u[c] - ubd[c]));
+  } else {
+    flux_dot_n(P, u, q, n, false, out);
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) st<S>(fh + ub + c * NF, plane_u, out[c]);
+}
+
+// --------------------------------------------------------------------------------------------
+// k_volume: pointwise flux and source, projection, lifting of F_hat, B^T -> nodal r (and J v)
+// --------------------------------------------------------------------------------------------
+template <typename S>
+__device__ __forceinline__ void volume_point(const Phys& P, const S u[5], const S q[3][5],
+                                             const double G[9], double Wd, const double acc[3],
+                                             const double* xg, double t, S Fref[3][5], S src[5]) {
+  Prim<S> w;
+  primitives(P, u, q, w);
+  const S cm = (P.c_mu * w.mu) * w.isr;
+  const S ck = ((P.c_k / P.cv) * w.mu) * w.isr;
+  S F[5][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[0][d] = u[0] * w.v[d];
+    F[4][d] = u[4] * w.v[d] - ck * w.gT[d];
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) F[1 + m][d] = u[1 + m] * w.v[d] - cm * w.eps[m][d];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) F[1 + m][m] = F[1 + m][m] + P.p_coef * u[4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fref[a][c] = G[a * 3 + 0] * F[c][0] + G[a * 3 + 1] * F[c][1] + G[a * 3 + 2] * F[c][2];
+  // source terms
+  const S sr = s_exp(0.5 * u[0]);
+  const S wxv[3] = {P.omega[1] * w.v[2] - P.omega[2] * w.v[1], P.omega[2] * w.v[0] - P.omega[0] * w.v[2],
+                    P.omega[0] * w.v[1] - P.omega[1] * w.v[0]};
+  src[0] = (u[0] - 1.0) * w.div;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const S a_m = acc[m] - P.cor * wxv[m];
+    const S eg = w.eps[m][0] * q[0][0] + w.eps[m][1] * q[1][0] + w.eps[m][2] * q[2][0];
+    src[1 + m] = sr * a_m + 0.5 * (w.div * u[1 + m]) - (0.5 * P.p_coef) * (u[4] * q[m][0]) + 0.5 * (cm * eg);
+  }
+  const S tg = w.gT[0] * q[0][0] + w.gT[1] * q[1][0] + w.gT[2] * q[2][0];
+  S diss = s_zero<S>();
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) diss = diss + w.eps[m][d] * w.gv[m][d];
+  S s4 = (1.5 - P.gamma) * (u[4] * w.div) + 0.5 * (ck * tg) + ((P.c_d / P.cv) * w.mu) * (w.isr * diss);
+  if (P.euv) {
+    const double r = sqrt(xg[0] * xg[0] + xg[1] * xg[1] + xg[2] * xg[2]);
+    const double sx = cos(P.euv_omega_t * t), sy = -sin(P.euv_omega_t * t);
+    double cchi = (xg[0] * sx + xg[1] * sy) / r;
+    cchi = fmin(1.0, fmax(-1.0, cchi));
+    const double chi = acos(cchi);
+    const double dz = (r - P.euv_r_peak) * P.euv_inv_w;
+    const double Qh = P.euv_amp * exp(-chi * chi * P.euv_inv2s2) * exp(-0.6931471805599453 * dz * dz);
+    s4 = s4 + (Qh / P.cv) * w.isr;
+  }
+  src[4] = s4;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) src[c] = src[c] * Wd;
+}
+
+template <int N, int NC>
+__global__ void k_volume(long long E, const Ops* __restrict__ ops, Phys P, double t,
+                         const double* __restrict__ geo, const double* __restrict__ accg,
+                         const double* __restrict__ xg, const double* __restrict__ ug,
+                         const double* __restrict__ qg, const double* __restrict__ fh,
+                         double* __restrict__ r, double* __restrict__ jv) {
+  using S = typename std::conditional<NC == 2, Dual, double>::type;
+  constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
+  __shared__ SmemOps so;
+  extern __shared__ double smem[];
+  double* sF = smem;                        // [EPB][3][C][NP]
+  double* sH = sF + EPB * 3 * C * NP;       // [EPB][6][C][NF]
+  double* sR = sH + EPB * 6 * C * NF;       // [EPB][C][NP]
+  double* sT = sR + EPB * C * NP;           // [EPB][C][NP]
+  load_ops<N>(ops, so);
+  const long long e0 = (long long)blockIdx.x * EPB;
+  const long long plane_f = E * 30 * NF;
+  for (int idx = threadIdx.x; idx < EPB * 30 * NF; idx += blockDim.x) {
+    const int l = idx / (30 * NF), rem = idx % (30 * NF);
+    const long long e = e0 + l;
+    if (e < E) {
+      const int phi = rem / (5 * NF), c = (rem / NF) % 5, f = rem % NF;
+      for (int pl = 0; pl < NC; ++pl)
+        sH[((l * 6 + phi) * C + 5 * pl + c) * NF + f] = fh[pl * plane_f + e * 30 * NF + rem];
+    }
+  }
+  const int el = threadIdx.x / NP, g = threadIdx.x % NP;
+  const long long e = e0 + el;
+  const bool active = el < EPB && e < E;
+  S srcv[5];
+  if (active) {
+    const long long plane_g = E * 5 * NP, plane_q = E * 15 * NP;
+    S u[5], q[3][5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u[c] = ld<S, NC>(ug + e * 5 * NP + c * NP + g, plane_g);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) q[d][c] = ld<S, NC>(qg + e * 15 * NP + (d * 5 + c) * NP + g, plane_q);
+    double G[9];
+    const double* gp = geo + e * 10 * NP + g;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) G[k] = gp[k * NP];
+    const double Wd = gp[9 * NP];
+    const double a3[3] = {accg[e * 3 * NP + g], accg[e * 3 * NP + NP + g], accg[e * 3 * NP + 2 * NP + g]};
+    double x3[3] = {0.0, 0.0, 0.0};
+    if (P.euv) {
+      x3[0] = xg[e * 3 * NP + g];
+      x3[1] = xg[e * 3 * NP + NP + g];
+      x3[2] = xg[e * 3 * NP + 2 * NP + g];
+    }
+    S Fref[3][5];
+    volume_point<S>(P, u, q, G, Wd, a3, x3, t, Fref, srcv);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        if constexpr (NC == 1) {
+          sF[((el * 3 + a) * C + c) * NP + g] = Fref[a][c];
+        } else {
+          sF[((el * 3 + a) * C + c) * NP + g] = Fref[a][c].v;
+          sF[((el * 3 + a) * C + 5 + c) * NP + g] = Fref[a][c].d;
+        }
+      }
+  }
+  __syncthreads();
+  if (active) {
+    for (int c = 0; c < C; ++c) {
+      double R;
+      if constexpr (NC == 1) R = srcv[c];
+      else R = (c < 5) ? srcv[c].v : srcv[c - 5].d;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) R += line<N, true>(so.D, sF + ((el * 3 + a) * C + c) * NP, g, a);
+#pragma unroll
+      for (int phi = 0; phi < 6; ++phi) {
+        const int axis = phi >> 1;
+        const double coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
+        R = fma(-coef, sH[((el * 6 + phi) * C + c) * NF + vol_face_point<N>(g, axis)], R);
+      }
+      sR[(el * C + c) * NP + g] = R;
+    }
+  }
+  __syncthreads();
+  double* in = sR;
+  double* out = sT;
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    if (active)
+      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, true>(so.B, in + (el * C + c) * NP, g, dir);
+    __syncthreads();
+    double* tt = in;
+    in = out;
+    out = tt;
+  }
+  for (int idx = threadIdx.x; idx < EPB * 5 * NP; idx += blockDim.x) {
+    const int l = idx / (5 * NP), rem = idx % (5 * NP);
+    const long long ee = e0 + l;
+    if (ee < E) {
+      if (r) r[ee * 5 * NP + rem] = in[(l * C) * NP + rem];
+      if (NC == 2) jv[ee * 5 * NP + rem] = in[(l * C + 5) * NP + rem];
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// tensor transforms of nodal q and the mass matrix
+// --------------------------------------------------------------------------------------------
+// out = A x A x A in (T: A^T) for C components per element, then optionally face traces of out
+template <int N, bool T, int C>
+__global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, const double* __restrict__ in_g,
+                         double* __restrict__ out_g, const double* __restrict__ weight,
+                         double* __restrict__ traces) {
+  constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF;
+  __shared__ SmemOps so;
+  extern __shared__ double smem[];
+  double* b0 = smem;
+  double* b1 = smem + C * NP;
+  load_ops<N>(ops, so);
+  const long long e = blockIdx.x;
+  const int g = threadIdx.x;
+  for (int idx = threadIdx.x; idx < C * NP; idx += blockDim.x) b0[idx] = in_g[e * C * NP + idx];
+  __syncthreads();
+  const double* A = (which == 0) ? so.B : so.Binv;
+  double* in = b0;
+  double* out = b1;
+  for (int dir = 0; dir < 3; ++dir) {
+    if (g < NP)
+      for (int c = 0; c < C; ++c) out[c * NP + g] = line<N, T>(A, in + c * NP, g, dir);
+    __syncthreads();
+    double* tt = in;
+    in = out;
+    out = tt;
+  }
+  if (weight) {
+    // mass matrix: W-weighted Gauss values, then back with B^T
+    if (g < NP) {
+      const double wd = weight[e * 10 * NP + 9 * NP + g];
+      for (int c = 0; c < C; ++c) in[c * NP + g] *= wd;
+    }
+    __syncthreads();
+    for (int dir = 0; dir < 3; ++dir) {
+      if (g < NP)
+        for (int c = 0; c < C; ++c) out[c * NP + g] = line<N, true>(A, in + c * NP, g, dir);
+      __syncthreads();
+      double* tt = in;
+      in = out;
+      out = tt;
+    }
+  }
+  for (int idx = threadIdx.x; idx < C * NP; idx += blockDim.x) out_g[e * C * NP + idx] = in[idx];
+  if (traces) {
+    for (int idx = threadIdx.x; idx < 6 * C * NF; idx += blockDim.x) {
+      const int phi = idx / (C * NF), c = (idx / NF) % C, f = idx % NF;
+      const double* ev = (phi & 1) ? so.eR : so.eL;
+      double acc = 0.0;
+      for (int k = 0; k < N; ++k) acc = fma(ev[k], in[c * NP + face_vol_point<N>(phi, f, k)], acc);
+      traces[e * 6 * C * NF + idx] = acc;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// geometry at Gauss points and face points (isoparametric map of the node coordinates)
+// --------------------------------------------------------------------------------------------
+template <int N>
+__global__ void k_geometry(long long E, const Ops* __restrict__ ops, Phys P, int gravity_kind,
+                           double g0, double g1, double g2, double g_r0,
+                           const double* __restrict__ x, double* __restrict__ geo,
+                           double* __restrict__ accg, double* __restrict__ xg, double* __restrict__ fgeo) {
+  constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF;
+  __shared__ SmemOps so;
+  __shared__ double w1[MAXN];
+  extern __shared__ double smem[];
+  double* b0 = smem;           // [3][NP]
+  double* b1 = b0 + 3 * NP;    // [3][NP]
+  double* J = b1 + 3 * NP;     // [9][NP] J[d][a]
+  load_ops<N>(ops, so);
+  if (threadIdx.x < N) w1[threadIdx.x] = ops->w[threadIdx.x];
+  const long long e = blockIdx.x;
+  const int g = threadIdx.x;
+  for (int idx = threadIdx.x; idx < 3 * NP; idx += blockDim.x) b0[idx] = x[e * 3 * NP + idx];
+  __syncthreads();
+  double* in = b0;
+  double* out = b1;
+  for (int dir = 0; dir < 3; ++dir) {
+    if (g < NP)
+      for (int c = 0; c < 3; ++c) out[c * NP + g] = line<N, false>(so.B, in + c * NP, g, dir);
+    __syncthreads();
+    double* tt = in;
+    in = out;
+    out = tt;
+  }
+  // in: Gauss point positions
+  if (g < NP) {
+    for (int d = 0; d < 3; ++d)
+      for (int a = 0; a < 3; ++a) J[(d * 3 + a) * NP + g] = line<N, false>(so.D, in + d * NP, g, a);
+  }
+  __syncthreads();
+  if (g < NP) {
+    double j[3][3];
+    for (int d = 0; d < 3; ++d)
+      for (int a = 0; a < 3; ++a) j[d][a] = J[(d * 3 + a) * NP + g];
+    // cofactors: cof[d][a] = d(det)/d j[d][a] = det * (J^{-1})[a][d]
+    double cof[3][3];
+    cof[0][0] = j[1][1] * j[2][2] - j[1][2] * j[2][1];
+    cof[0][1] = j[1][2] * j[2][0] - j[1][0] * j[2][2];
+    cof[0][2] = j[1][0] * j[2][1] - j[1][1] * j[2][0];
+    cof[1][0] = j[0][2] * j[2][1] - j[0][1] * j[2][2];
+    cof[1][1] = j[0][0] * j[2][2] - j[0][2] * j[2][0];
+    cof[1][2] = j[0][1] * j[2][0] - j[0][0] * j[2][1];
+    cof[2][0] = j[0][1] * j[1][2] - j[0][2] * j[1][1];
+    cof[2][1] = j[0][2] * j[1][0] - j[0][0] * j[1][2];
+    cof[2][2] = j[0][0] * j[1][1] - j[0][1] * j[1][0];
+    const double det = j[0][0] * cof[0][0] + j[0][1] * cof[0][1] + j[0][2] * cof[0][2];
+    const int i0 = g % N, i1 = (g / N) % N, i2 = g / (N * N);
+    const double wq = w1[i0] * w1[i1] * w1[i2];
+    double* gp = geo + e * 10 * NP + g;
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) gp[(a * 3 + d) * NP] = wq * cof[d][a];
+    gp[9 * NP] = wq * det;
+    const double X[3] = {in[g], in[NP + g], in[2 * NP + g]};
+    for (int d = 0; d < 3; ++d) xg[e * 3 * NP + d * NP + g] = X[d];
+    double gv[3];
+    if (gravity_kind == 0) {
+      gv[0] = g0; gv[1] = g1; gv[2] = g2;
+    } else {
+      const double rr = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+      const double fac = -(g_r0 / rr) * (g_r0 / rr) / rr;
+      for (int d = 0; d < 3; ++d) gv[d] = fac * X[d];
+    }
+    const double* w = P.omega;
+    const double wx[3] = {w[1] * X[2] - w[2] * X[1], w[2] * X[0] - w[0] * X[2], w[0] * X[1] - w[1] * X[0]};
+    const double wwx[3] = {w[1] * wx[2] - w[2] * wx[1], w[2] * wx[0] - w[0] * wx[2], w[0] * wx[1] - w[1] * wx[0]};
+    const double cen = (P.cor * P.cor * 0.25);   // Fr^2 (cor = 2 Fr / sqrt(gamma))
+    for (int d = 0; d < 3; ++d) accg[e * 3 * NP + d * NP + g] = gv[d] / P.gamma - cen * wwx[d];
+  }
+  // faces: extrapolate the tangential Jacobian columns, n dS = side * (J_{a+1} x J_{a+2})
+  for (int idx = threadIdx.x; idx < 6 * NF; idx += blockDim.x) {
+    const int phi = idx / NF, f = idx % NF;
+    const int axis = phi >> 1;
+    const double side = (phi & 1) ? 1.0 : -1.0;
+    const double* ev = (phi & 1) ? so.eR : so.eL;
+    const int a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
+    double t1[3], t2[3];
+    for (int d = 0; d < 3; ++d) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int k = 0; k < N; ++k) {
+        const int gg = face_vol_point<N>(phi, f, k);
+        s1 = fma(ev[k], J[(d * 3 + a1) * NP + gg], s1);
+        s2 = fma(ev[k], J[(d * 3 + a2) * NP + gg], s2);
+      }
+      t1[d] = s1;
+      t2[d] = s2;
+    }
+    double nv[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2], t1[0] * t2[1] - t1[1] * t2[0]};
+    const int is = f % N, it = f / N;
+    const double wf = w1[is] * w1[it];
+    double* fp = fgeo + ((e * 6 + phi) * 4) * NF + f;
+    double a2n = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      fp[d * NF] = wf * side * nv[d];
+      a2n += nv[d] * nv[d];
+    }
+    fp[3 * NF] = wf * sqrt(a2n);
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// Driver
+// --------------------------------------------------------------------------------------------
+template <int N, int NC>
+struct Smem {
+  static constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
+  static constexpr size_t interp = sizeof(double) * (2 * EPB * C * NP);
+  static constexpr size_t grad = sizeof(double) * (EPB * (C * NP + 6 * C * NF + 18 * NF + 9 * NP + 3 * C * NP));
+  static constexpr size_t volume = sizeof(double) * (EPB * (3 * C * NP + 6 * C * NF + 2 * C * NP));
+};
+
+template <typename K>
+static int set_smem(K kernel, size_t bytes) {
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (err != cudaSuccess) return fail(DG_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
+  return DG_OK;
+}
+
+template <int N, int NC>
+static int run_interp(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
+  constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
+  const size_t sm = Smem<N, NC>::interp;
+  int rc = set_smem(k_interp<N, NC>, sm);
+  if (rc) return rc;
+  const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
+  prof_begin(m, s, KK_INTERP);
+  k_interp<N, NC><<<blocks, EPB * NP, sm, s>>>(u, v, m->E, m->d_ops, m->ws.ug, m->ws.uf);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_interp");
+  return DG_OK;
+}
+
+template <int N, int NC>
+static int run_grad(dg_mesh* m, cudaStream_t s) {
+  constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
+  const size_t sm = Smem<N, NC>::grad;
+  int rc = set_smem(k_grad<N, NC>, sm);
+  if (rc) return rc;
+  const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
+  prof_begin(m, s, KK_GRAD);
+  k_grad<N, NC><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, m->phys, m->geo, m->fgeo, m->nbr, m->nbr_fo,
+                                              m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_grad");
+  return DG_OK;
+}
+
+template <int N, int NC>
+static int run_faces(dg_mesh* m, cudaStream_t s) {
+  constexpr int NF = Shape<N>::NF;
+  const long long work = m->nfaces * NF;
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((work + threads - 1) / threads);
+  prof_begin(m, s, KK_FACES);
+  k_faces<N, NC><<<blocks, threads, 0, s>>>(m->E, m->nfaces, m->phys, m->face_e, m->face_f, m->nbr, m->nbr_fo,
+                                             m->fgeo, m->ws.uf, m->ws.qf, m->ws.fh);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_faces");
+  return DG_OK;
+}
+
+template <int N, int NC>
+static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t s) {
+  constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
+  const size_t sm = Smem<N, NC>::volume;
+  int rc = set_smem(k_volume<N, NC>, sm);
+  if (rc) return rc;
+  const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
+  prof_begin(m, s, KK_VOLUME);
+  k_volume<N, NC><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, m->phys, t, m->geo, m->acc, m->xg, m->ws.ug,
+                                                m->ws.qg, m->ws.fh, r, jv);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_volume");
+  return DG_OK;
+}
+
+template <int N>
+int Driver<N>::geometry(dg_mesh* m, cudaStream_t s) {
+  constexpr int NP = Shape<N>::NP;
+  const size_t sm = sizeof(double) * 15 * NP;
+  int rc = set_smem(k_geometry<N>, sm);
+  if (rc) return rc;
+  const dg_mesh_desc& d = m->desc;
+  prof_begin(m, s, KK_GEOMETRY);
+  k_geometry<N><<<(unsigned)m->E, NP < 32 ? 32 : NP, sm, s>>>(m->E, m->d_ops, m->phys, d.gravity_kind, d.gvec[0],
+                                                            d.gvec[1], d.gvec[2], d.g_r0, m->x, m->geo, m->acc,
+                                                            m->xg, m->fgeo);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_geometry");
+  return DG_OK;
+}
+
+template <int N>
+int Driver<N>::gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
+  int rc = v ? run_interp<N, 2>(m, u, v, s) : run_interp<N, 1>(m, u, nullptr, s);
+  if (rc) return rc;
+  return v ? run_grad<N, 2>(m, s) : run_grad<N, 1>(m, s);
+}
+
+template <int N>
+int Driver<N>::residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
+                        bool tangent, cudaStream_t s) {
+  (void)u;
+  (void)v;
+  int rc = tangent ? run_faces<N, 2>(m, s) : run_faces<N, 1>(m, s);
+  if (rc) return rc;
+  return tangent ? run_volume<N, 2>(m, t, r, jv, s) : run_volume<N, 1>(m, t, r, nullptr, s);
+}
+
+template <int N>
+int Driver<N>::q_to_nodal(dg_mesh* m, double* q, cudaStream_t s) {
+  constexpr int NP = Shape<N>::NP;
+  const size_t sm = sizeof(double) * 2 * 15 * NP;
+  int rc = set_smem(k_tensor<N, false, 15>, sm);
+  if (rc) return rc;
+  prof_begin(m, s, KK_TENSOR);
+  k_tensor<N, false, 15><<<(unsigned)m->E, NP < 32 ? 32 : NP, sm, s>>>(m->E, m->d_ops, 1, m->ws.qg, q, nullptr,
+                                                                      nullptr);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_tensor(q nodal)");
+  return DG_OK;
+}
+
+template <int N>
+int Driver<N>::q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) {
+  constexpr int NP = Shape<N>::NP;
+  const size_t sm = sizeof(double) * 2 * 15 * NP;
+  int rc = set_smem(k_tensor<N, false, 15>, sm);
+  if (rc) return rc;
+  prof_begin(m, s, KK_TENSOR);
+  k_tensor<N, false, 15><<<(unsigned)m->E, NP < 32 ? 32 : NP, sm, s>>>(m->E, m->d_ops, 0, q, m->ws.qg, nullptr,
+                                                                      m->ws.qf);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_tensor(q gauss)");
+  return DG_OK;
+}
+
+template <int N>
+int Driver<N>::mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s) {
+  constexpr int NP = Shape<N>::NP;
+  const size_t sm = sizeof(double) * 2 * 5 * NP;
+  int rc = set_smem(k_tensor<N, false, 5>, sm);
+  if (rc) return rc;
+  prof_begin(m, s, KK_TENSOR);
+  k_tensor<N, false, 5><<<(unsigned)m->E, NP < 32 ? 32 : NP, sm, s>>>(m->E, m->d_ops, 0, v, mv, m->geo, nullptr);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_tensor(mass)");
+  return DG_OK;
+}
+
+}  // namespace dg

@@ -1,0 +1,194 @@
+"""Thin Python binding of the C ABI in include/dg.h (argument marshalling only).
+
+Every operation runs in the CUDA library libdg_gb300.so; there is no CPU path. Tensors are torch
+CUDA float64 tensors in the layouts documented in include/dg.h; calls are ordered on torch's
+current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libdg_gb300.so")
+HEADER = os.path.join(HERE, "..", "include", "dg.h")
+
+DG_JV_EXACT = 0
+DG_JV_FD = 1
+
+
+class DgMeshDesc(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("p", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32), ("bc_lo", ctypes.c_int32), ("bc_hi", ctypes.c_int32),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("h_first", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("grashof", ctypes.c_double), ("prandtl", ctypes.c_double),
+        ("mass", ctypes.c_double), ("visc_exp", ctypes.c_double), ("lambda0", ctypes.c_double),
+        ("t_wall", ctypes.c_double), ("gravity_kind", ctypes.c_int32), ("euv", ctypes.c_int32),
+        ("gvec", ctypes.c_double * 3), ("g_r0", ctypes.c_double), ("omega", ctypes.c_double * 3),
+        ("froude", ctypes.c_double), ("euv_amp", ctypes.c_double), ("euv_sigma", ctypes.c_double),
+        ("euv_r_peak", ctypes.c_double), ("euv_width", ctypes.c_double), ("euv_omega_t", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def declared_functions():
+    """Names of the functions declared in include/dg.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(dg_[a-z_0-9]+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """Load libdg_gb300.so (raises if it was not built: the library has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library missing at {LIB_PATH}; run paper_2306_01085_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, i32, i64p, d = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_double
+    L.dg_last_error.restype = ctypes.c_char_p
+    L.dg_mesh_create.argtypes = [ctypes.POINTER(DgMeshDesc), ctypes.POINTER(vp)]
+    L.dg_mesh_destroy.argtypes = [vp]
+    L.dg_mesh_destroy.restype = None
+    L.dg_mesh_sizes.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_int32), i64p]
+    L.dg_mesh_nodes.argtypes = [vp, dp, vp]
+    L.dg_gradient.argtypes = [vp, dp, dp, vp]
+    L.dg_residual.argtypes = [vp, dp, dp, d, dp, vp]
+    L.dg_jvp.argtypes = [vp, dp, dp, d, i32, d, dp, dp, vp]
+    L.dg_mass_apply.argtypes = [vp, dp, dp, vp]
+    L.dg_profile_start.argtypes = [vp, i32]
+    L.dg_profile_stop.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i64p]
+    L.dg_kernel_name.argtypes = [i32]
+    L.dg_kernel_name.restype = ctypes.c_char_p
+    L.dg_probe_fp64.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    _lib = L
+    return L
+
+
+class DgError(RuntimeError):
+    pass
+
+
+def _check(rc):
+    if rc != 0:
+        raise DgError(f"dg error {rc}: {lib().dg_last_error().decode()}")
+
+
+def to_c_desc(desc: W.MeshDesc) -> DgMeshDesc:
+    c = DgMeshDesc()
+    for name, _ in DgMeshDesc._fields_:
+        val = getattr(desc, name)
+        if name in ("gvec", "omega"):
+            getattr(c, name)[:] = [float(x) for x in val]
+        else:
+            setattr(c, name, val)
+    return c
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, shape=None, name="tensor"):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise DgError(f"{name} must be a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise DgError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A library mesh: geometry, connectivity and workspace on the current CUDA device."""
+
+    def __init__(self, desc: W.MeshDesc):
+        self.desc = desc
+        self._c = to_c_desc(desc)
+        h = ctypes.c_void_p()
+        _check(lib().dg_mesh_create(ctypes.byref(self._c), ctypes.byref(h)))
+        self._h = h
+        ne, npe, nd = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().dg_mesh_sizes(h, ctypes.byref(ne), ctypes.byref(npe), ctypes.byref(nd)))
+        self.n_elem, self.n_p, self.n_dof = ne.value, npe.value, nd.value
+        self.u_shape = (self.n_elem, 5, self.n_p)
+        self.q_shape = (self.n_elem, 3, 5, self.n_p)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dg_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, shape=None):
+        import torch
+        return torch.empty(shape or self.u_shape, dtype=torch.float64, device="cuda")
+
+    def nodes(self):
+        x = self.empty((self.n_elem, 3, self.n_p))
+        _check(lib().dg_mesh_nodes(self._h, _ptr(x), _stream()))
+        return x
+
+    def gradient(self, u, out=None):
+        q = out if out is not None else self.empty(self.q_shape)
+        _check(lib().dg_gradient(self._h, _ptr(u, self.u_shape, "u"), _ptr(q, self.q_shape, "q"), _stream()))
+        return q
+
+    def residual(self, u, q=None, t=0.0, out=None):
+        r = out if out is not None else self.empty()
+        _check(lib().dg_residual(self._h, _ptr(u, self.u_shape, "u"), _ptr(q, self.q_shape, "q"), float(t),
+                                 _ptr(r, self.u_shape, "r"), _stream()))
+        return r
+
+    def jvp(self, u, v, t=0.0, mode="exact", eps=0.0, out=None, r_out=None):
+        jv = out if out is not None else self.empty()
+        m = DG_JV_EXACT if mode == "exact" else DG_JV_FD
+        _check(lib().dg_jvp(self._h, _ptr(u, self.u_shape, "u"), _ptr(v, self.u_shape, "v"), float(t), m,
+                            float(eps), _ptr(jv, self.u_shape, "jv"), _ptr(r_out, self.u_shape, "r_out"),
+                            _stream()))
+        return jv
+
+    def mass(self, v, out=None):
+        mv = out if out is not None else self.empty()
+        _check(lib().dg_mass_apply(self._h, _ptr(v, self.u_shape, "v"), _ptr(mv, self.u_shape, "mv"), _stream()))
+        return mv
+
+    # -- tracing ---------------------------------------------------------------------------
+    def profile_start(self, capacity=4096):
+        _check(lib().dg_profile_start(self._h, int(capacity)))
+
+    def profile_stop(self, n_kinds=32):
+        """Per kernel kind: (total device ms, launches) of the traced launches, and total launches."""
+        ms = (ctypes.c_double * n_kinds)()
+        cnt = (ctypes.c_int32 * n_kinds)()
+        tot = ctypes.c_int64()
+        _check(lib().dg_profile_stop(self._h, n_kinds, ms, cnt, ctypes.byref(tot)))
+        out = {}
+        for k in range(n_kinds):
+            name = lib().dg_kernel_name(k).decode()
+            if name and cnt[k]:
+                out[name] = (ms[k], cnt[k])
+        return out, tot.value
+
+
+def probe_fp64():
+    """Achieved FP64 FMA throughput of the device in TFLOP/s (library probe kernel)."""
+    t = ctypes.c_double()
+    _check(lib().dg_probe_fp64(ctypes.byref(t)))
+    return t.value

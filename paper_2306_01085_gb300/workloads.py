@@ -243,8 +243,22 @@ def fourier_field(seed: int, stream: int, xs: np.ndarray, kmax=3) -> np.ndarray:
     nk = ks.shape[0]
     ab = 2.0 * uniform01(seed, 2 * nk, offset=stream * 4096) - 1.0
     a, b = ab[:nk], ab[nk:]
-    phase = 2.0 * np.pi * np.tensordot(xs, ks.T, axes=([-1], [0]))
-    f = np.cos(phase) @ a + np.sin(phase) @ b
+    # exp(2 pi i k.x) as a product of per-axis powers of exp(2 pi i x_d)
+    flat = xs.reshape(-1, 3)
+    base = [np.exp(2j * np.pi * flat[:, d]) for d in range(3)]
+    pw = []
+    for d in range(3):
+        tab = {0: np.ones(flat.shape[0], dtype=np.complex128)}
+        for j in range(1, kmax + 1):
+            tab[j] = tab[j - 1] * base[d]
+            tab[-j] = np.conj(tab[j])
+        pw.append(tab)
+    f = np.zeros(flat.shape[0])
+    for k in range(nk):
+        k0, k1, k2 = (int(c) for c in ks[k])
+        z = pw[0][k0] * pw[1][k1] * pw[2][k2]
+        f += a[k] * z.real + b[k] * z.imag
+    f = f.reshape(xs.shape[:-1])
     return f / (np.abs(a).sum() + np.abs(b).sum())
 
 
@@ -314,7 +328,6 @@ def shell_state(x: np.ndarray, desc: MeshDesc, seed: int = 2, ref: Reference | N
     T = T_d / ref.T0 * (1.0 + t_amp * fT)
     v = np.stack([v_ms / ref.a0 * f for f in fv])
     rho = rho_d / ref.rho0
-    v = np.moveaxis(v, 0, 0)
     return pack_state(rho, v, T)
 
 
