@@ -82,14 +82,18 @@ typedef struct dg_mesh dg_mesh;
 const char* dg_last_error(void);
 
 /*
- * Build the mesh (Sec. 3.3 cubed sphere with geometric radial growth, or a box), its face
- * connectivity, and the isoparametric geometry at the quadrature points (Sec. 3.1: k-th degree
- * curved elements; (p+1)^3 Gauss points per element, (p+1)^2 per face). Allocates all library
- * storage on the current device and synchronises it. *out receives an opaque handle to release
- * with dg_mesh_destroy. Errors: DG_EINVAL (p outside 1..4, non-positive sizes, inconsistent
- * boundaries), DG_ENOMEM, DG_ECUDA.
+ * Build the mesh, its face connectivity, and the isoparametric geometry at the quadrature points
+ * (Sec. 3.1: k-th degree curved elements; (p+1)^3 Gauss points per element, (p+1)^2 per face).
+ * nodes: optional HOST array [n_elem][3][n_p] of GLL node coordinates in the numbering above (the
+ * mesh as input data, read during the call only); NULL generates them from desc (Sec. 3.3 cubed
+ * sphere with geometric radial growth from h_first, or the box). Faces are matched from the node
+ * coordinates (corner nodes, periodic in x and y for boxes, and z when bc_lo is periodic); faces
+ * left unmatched take bc_lo (box z = 0 / inner sphere) or bc_hi. Allocates all library storage on
+ * the current device and synchronises it. *out receives an opaque handle to release with
+ * dg_mesh_destroy. Errors: DG_EINVAL (p outside 1..4, non-positive sizes, inconsistent
+ * boundaries, faces that do not match), DG_ENOMEM, DG_ECUDA.
  */
-int dg_mesh_create(const dg_mesh_desc* desc, dg_mesh** out);
+int dg_mesh_create(const dg_mesh_desc* desc, const double* nodes, dg_mesh** out);
 
 /* Release every library allocation of the mesh (synchronises the device). NULL is ignored. */
 void dg_mesh_destroy(dg_mesh* mesh);

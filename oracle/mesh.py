@@ -1,16 +1,15 @@
-"""Meshes, isoparametric geometry and face matching (oracle; test infrastructure only).
+"""Isoparametric geometry and face matching of a mesh given by its node coordinates (oracle; test
+infrastructure only).
 
-Sec. 3.1 uses k-th degree curved elements; Sec. 3.3 uses cubed-sphere shells with geometric radial
-growth from a first-layer height. The map of every element is the degree-k polynomial interpolant
-of its GLL node positions (isoparametric). Conventions shared with the library (stated in
-include/dg.h, implemented separately on each side):
+Sec. 3.1 uses k-th degree curved elements: the map of every element is the degree-k polynomial
+interpolant of its GLL node positions X[e, d, i] (node i = a + n b + n^2 c, a along xi_1). The
+node positions themselves are an input (the workload's mesh, from paper_2306_01085_gb300.workloads);
+everything derived from them here (Jacobians, normals, neighbours) is computed independently of the
+library.
 
-  box   element e = i + nx (j + ny k); nodes at x = (i + (1 + xi_a)/2) lx/nx, ...
-  shell element e = k + nz (i + n (j + n P)) for panel P, angular cell (i, j), radial layer k;
-        equiangular gnomonic panels: direction c_P + tan(alpha) a_P + tan(beta) b_P, normalised,
-        alpha, beta in [-pi/4, pi/4]; panels (c, a, b) =
-        (+x,+y,+z) (+y,-x,+z) (-x,-y,+z) (-y,+x,+z) (+z,+y,-x) (-z,+y,+x).
-  node  i = a + n b + n^2 c (a along xi_1, the fastest), n = k+1.
+Jacobians are taken of X - X[:, :, 0] (the element's first node): the derivatives of the basis sum
+to zero, so this is the same quantity, but its rounding is relative to the element size rather than
+to |x| (a 2.5 km layer at 6471 km radius would otherwise lose four digits).
 
 Face matching is done here by brute force on physical coordinates (face centres, then nearest face
 quadrature point), independently of the library's bookkeeping.
@@ -23,82 +22,11 @@ import math
 import numpy as np
 from scipy.spatial import cKDTree
 
+from paper_2306_01085_gb300 import workloads as W
+
 from . import quadrature as Q
 
-PANELS = [
-    ((1, 0, 0), (0, 1, 0), (0, 0, 1)),
-    ((0, 1, 0), (-1, 0, 0), (0, 0, 1)),
-    ((-1, 0, 0), (0, -1, 0), (0, 0, 1)),
-    ((0, -1, 0), (1, 0, 0), (0, 0, 1)),
-    ((0, 0, 1), (0, 1, 0), (-1, 0, 0)),
-    ((0, 0, -1), (0, 1, 0), (1, 0, 0)),
-]
-
 BC_INTERIOR, BC_WALL, BC_OUTFLOW = 0, 1, 2
-
-
-def radial_layers(r_in, r_out, nz, h_first):
-    """Layer interfaces r_0 = r_in < ... < r_nz = r_out with heights h_first q^k (Sec. 3.3).
-
-    The growth ratio q solves sum_{k<nz} h_first q^k = r_out - r_in (bisection); h_first <= 0 gives
-    uniform layers.
-    """
-    total = r_out - r_in
-    if h_first <= 0.0 or nz == 1:
-        return r_in + total * np.arange(nz + 1) / nz
-    def excess(q):
-        return h_first * sum(q ** k for k in range(nz)) - total
-    lo, hi = 1.0, 2.0
-    if excess(lo) > 0:
-        lo, hi = 1e-6, 1.0
-    while excess(hi) < 0:
-        hi *= 2.0
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        if excess(mid) > 0:
-            hi = mid
-        else:
-            lo = mid
-    q = 0.5 * (lo + hi)
-    r = r_in + np.concatenate([[0.0], np.cumsum(h_first * q ** np.arange(nz))])
-    r[-1] = r_out
-    return r
-
-
-def node_coordinates(desc):
-    """GLL node positions X[e, d, i] of every element (isoparametric node set)."""
-    n = desc.p + 1
-    xi, _ = Q.gll(n)
-    ref = Q.tensor_points(xi)          # (n^3, 3): (xi_a, xi_b, xi_c)
-    s = 0.5 * (1.0 + ref)              # in [0, 1]
-    if desc.kind == 0:
-        hx, hy, hz = desc.lx / desc.nx, desc.ly / desc.ny, desc.lz / desc.nz
-        X = np.zeros((desc.n_elem, 3, n ** 3))
-        for k in range(desc.nz):
-            for j in range(desc.ny):
-                for i in range(desc.nx):
-                    e = i + desc.nx * (j + desc.ny * k)
-                    X[e, 0] = (i + s[:, 0]) * hx
-                    X[e, 1] = (j + s[:, 1]) * hy
-                    X[e, 2] = (k + s[:, 2]) * hz
-        return X
-    nn, nz = desc.nx, desc.nz
-    rl = radial_layers(desc.r_inner, desc.r_outer, nz, desc.h_first)
-    d_ang = 0.5 * math.pi / nn
-    X = np.zeros((desc.n_elem, 3, n ** 3))
-    for P, (c, a, b) in enumerate(PANELS):
-        c, a, b = np.array(c, float), np.array(a, float), np.array(b, float)
-        for j in range(nn):
-            for i in range(nn):
-                alpha = -0.25 * math.pi + (i + s[:, 0]) * d_ang
-                beta = -0.25 * math.pi + (j + s[:, 1]) * d_ang
-                dirv = c[:, None] + np.tan(alpha)[None, :] * a[:, None] + np.tan(beta)[None, :] * b[:, None]
-                dirv = dirv / np.sqrt((dirv ** 2).sum(0))[None, :]
-                for k in range(nz):
-                    e = k + nz * (i + nn * (j + nn * P))
-                    r = rl[k] + s[:, 2] * (rl[k + 1] - rl[k])
-                    X[e] = dirv * r[None, :]
-    return X
 
 
 class OracleMesh:
@@ -121,7 +49,7 @@ class OracleMesh:
             self.phiF.append(ph)
             self.dphiF.append(dph)
         self.wF = np.einsum("b,a->ba", self.wg, self.wg).ravel()
-        self.X = node_coordinates(desc) if X is None else X
+        self.X = W.mesh_nodes(desc) if X is None else X
         self.n_elem = self.X.shape[0]
         self._geometry()
         self._connect()
@@ -129,14 +57,15 @@ class OracleMesh:
     # -- geometry ---------------------------------------------------------------------------
     def _geometry(self):
         X = self.X
+        Xr = X - X[:, :, :1]                                           # relative to the first node
         # J[e, g, d, a] = d x_d / d xi_a at volume Gauss points
-        J = np.einsum("edi,gai->egda", X, self.dphi)
+        J = np.einsum("edi,gai->egda", Xr, self.dphi)
         self.detJ = np.linalg.det(J)
         self.Jinv = np.linalg.inv(J)                                   # [e, g, a, d] = d xi_a / d x_d
         self.xG = np.einsum("edi,gi->edg", X, self.phi)
         nF, xF = [], []
         for f, (axis, side) in enumerate(Q.FACES):
-            Jf = np.einsum("edi,gai->egda", X, self.dphiF[f])
+            Jf = np.einsum("edi,gai->egda", Xr, self.dphiF[f])
             t1 = Jf[..., (axis + 1) % 3]
             t2 = Jf[..., (axis + 2) % 3]
             nF.append(side * np.moveaxis(np.cross(t1, t2), -1, 1))    # (e, 3, f) outward n dS

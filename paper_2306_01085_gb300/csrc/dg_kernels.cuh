@@ -616,7 +616,12 @@ __global__ void k_geometry(long long E, const Ops* __restrict__ ops, Phys P, int
   if (threadIdx.x < N) w1[threadIdx.x] = ops->w[threadIdx.x];
   const long long e = blockIdx.x;
   const int g = threadIdx.x;
-  for (int idx = threadIdx.x; idx < 3 * NP; idx += blockDim.x) b0[idx] = x[e * 3 * NP + idx];
+  // positions relative to the element's first node: the Jacobian is unchanged (derivatives of the
+  // basis sum to zero) and its rounding is relative to the element size instead of |x|
+  for (int idx = threadIdx.x; idx < 3 * NP; idx += blockDim.x) {
+    const int c = idx / NP;
+    b0[idx] = x[e * 3 * NP + idx] - x[e * 3 * NP + c * NP];
+  }
   __syncthreads();
   double* in = b0;
   double* out = b1;
@@ -628,7 +633,7 @@ __global__ void k_geometry(long long E, const Ops* __restrict__ ops, Phys P, int
     in = out;
     out = tt;
   }
-  // in: Gauss point positions
+  // in: Gauss point positions relative to the first node
   if (g < NP) {
     for (int d = 0; d < 3; ++d)
       for (int a = 0; a < 3; ++a) J[(d * 3 + a) * NP + g] = line<N, false>(so.D, in + d * NP, g, a);
@@ -656,7 +661,7 @@ __global__ void k_geometry(long long E, const Ops* __restrict__ ops, Phys P, int
     for (int a = 0; a < 3; ++a)
       for (int d = 0; d < 3; ++d) gp[(a * 3 + d) * NP] = wq * cof[d][a];
     gp[9 * NP] = wq * det;
-    const double X[3] = {in[g], in[NP + g], in[2 * NP + g]};
+    const double X[3] = {x[e * 3 * NP] + in[g], x[e * 3 * NP + NP] + in[NP + g], x[e * 3 * NP + 2 * NP] + in[2 * NP + g]};
     for (int d = 0; d < 3; ++d) xg[e * 3 * NP + d * NP + g] = X[d];
     double gv[3];
     if (gravity_kind == 0) {

@@ -113,7 +113,7 @@ void face_corner_ref(int phi, int cs, int ct, double out[3]) {
 
 }  // namespace
 
-static int build_connectivity(dg_mesh* m, const MapParams& mp, std::vector<int32_t>& nbr,
+static int build_connectivity(dg_mesh* m, const std::vector<double>& X, std::vector<int32_t>& nbr,
                               std::vector<int32_t>& nbr_fo, std::vector<int32_t>& face_e,
                               std::vector<int32_t>& face_f) {
   const dg_mesh_desc& d = m->desc;
@@ -146,20 +146,24 @@ static int build_connectivity(dg_mesh* m, const MapParams& mp, std::vector<int32
     }
     return s;
   };
-  // corners and centres of all faces
-  std::vector<double> corners((size_t)E * 6 * 4 * 3), centres((size_t)E * 6 * 3);
+  // corner nodes (the GLL nodes include the element corners) and centres of all faces
+  const int np = n * n * n;
+  std::vector<double> corners((size_t)E * 6 * 4 * 3), centres((size_t)E * 6 * 3), raw((size_t)E * 6 * 3);
   for (long long e = 0; e < E; ++e)
     for (int phi = 0; phi < 6; ++phi) {
       double cen[3] = {0, 0, 0};
       for (int k = 0; k < 4; ++k) {
-        double ref[3], p[3];
+        double ref[3];
         face_corner_ref(phi, k & 1, k >> 1, ref);
-        map_point(mp, e, ref[0], ref[1], ref[2], p);
+        const int ia = ref[0] > 0 ? n - 1 : 0, ib = ref[1] > 0 ? n - 1 : 0, ic = ref[2] > 0 ? n - 1 : 0;
+        const int node = ia + n * (ib + n * ic);
         for (int a = 0; a < 3; ++a) {
-          corners[((e * 6 + phi) * 4 + k) * 3 + a] = p[a];
-          cen[a] += 0.25 * p[a];
+          const double p = X[((size_t)e * 3 + a) * np + node];
+          corners[((e * 6 + phi) * 4 + k) * 3 + a] = p;
+          cen[a] += 0.25 * p;
         }
       }
+      for (int a = 0; a < 3; ++a) raw[(e * 6 + phi) * 3 + a] = cen[a];
       wrap(cen);
       for (int a = 0; a < 3; ++a) centres[(e * 6 + phi) * 3 + a] = cen[a];
     }
@@ -201,10 +205,18 @@ static int build_connectivity(dg_mesh* m, const MapParams& mp, std::vector<int32
     }
   }
   // orientation codes and boundary kinds
+  // the neighbour face is the own face moved by the exact translation between the two centres
+  // (zero except across a periodic boundary), so corners are matched without wrapping
   auto corner_match = [&](long long k_own, int corner, long long k_oth) {
     const double* p = &corners[(k_own * 4 + corner) * 3];
-    for (int j = 0; j < 4; ++j)
-      if (wdist2(p, &corners[(k_oth * 4 + j) * 3]) < tol * tol) return j;
+    double q[3];
+    for (int a = 0; a < 3; ++a) q[a] = p[a] + (raw[k_oth * 3 + a] - raw[k_own * 3 + a]);
+    for (int j = 0; j < 4; ++j) {
+      const double* c = &corners[(k_oth * 4 + j) * 3];
+      double d2 = 0.0;
+      for (int a = 0; a < 3; ++a) d2 += (c[a] - q[a]) * (c[a] - q[a]);
+      if (d2 < tol * tol) return j;
+    }
     return -1;
   };
   face_e.clear();
@@ -289,7 +301,7 @@ using namespace dg;
 
 extern "C" const char* dg_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" int dg_mesh_create(const dg_mesh_desc* desc, dg_mesh** out) {
+extern "C" int dg_mesh_create(const dg_mesh_desc* desc, const double* nodes, dg_mesh** out) {
   if (!desc || !out) return fail(DG_EINVAL, "dg_mesh_create: null argument");
   *out = nullptr;
   const dg_mesh_desc& d = *desc;
@@ -338,15 +350,45 @@ extern "C" int dg_mesh_create(const dg_mesh_desc* desc, dg_mesh** out) {
   std::vector<double> layers = (d.kind == DG_KIND_SHELL) ? radial_layers(d.r_inner, d.r_outer, d.nz, d.h_first)
                                                          : std::vector<double>(2, 0.0);
   MapParams mp{d.kind, d.nx, d.ny, d.nz, d.lx, d.ly, d.lz, layers.data()};
+  const long long E = m->E, NP = m->np, NF = m->nf;
+  int rc = 0;
+  rc |= dalloc(&m->x, E * 3 * NP);
+  if (rc) { free_mesh(m); return DG_ENOMEM; }
+  std::vector<double> X((size_t)E * 3 * NP);
+  if (nodes) {
+    std::memcpy(X.data(), nodes, sizeof(double) * X.size());
+    cudaError_t e1 = cudaMemcpy(m->x, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice);
+    if (e1 != cudaSuccess) { free_mesh(m); return fail(DG_ECUDA, std::string("node upload: ") + cudaGetErrorString(e1)); }
+  } else {
+    // nodes of the analytic map at the GLL points, on the device
+    double* d_layers = nullptr;
+    double* d_xi = nullptr;
+    if (dalloc(&d_layers, layers.size()) || dalloc(&d_xi, MAXN)) {
+      if (d_layers) cudaFree(d_layers);
+      free_mesh(m);
+      return DG_ENOMEM;
+    }
+    cudaError_t e1 = cudaMemcpy(d_layers, layers.data(), sizeof(double) * layers.size(), cudaMemcpyHostToDevice);
+    if (e1 == cudaSuccess) e1 = cudaMemcpy(d_xi, m->ops.xi, sizeof(double) * MAXN, cudaMemcpyHostToDevice);
+    MapParams mpd = mp;
+    mpd.r_layers = d_layers;
+    if (e1 == cudaSuccess) {
+      k_nodes<<<(unsigned)((E * NP + 255) / 256), 256>>>(mpd, E, m->n, d_xi, m->x);
+      e1 = cudaGetLastError();
+    }
+    if (e1 == cudaSuccess) e1 = cudaMemcpy(X.data(), m->x, sizeof(double) * X.size(), cudaMemcpyDeviceToHost);
+    cudaFree(d_layers);
+    cudaFree(d_xi);
+    if (e1 != cudaSuccess) { free_mesh(m); return fail(DG_ECUDA, std::string("node kernel: ") + cudaGetErrorString(e1)); }
+  }
   std::vector<int32_t> nbr, nbr_fo, face_e, face_f;
-  int rc = build_connectivity(m, mp, nbr, nbr_fo, face_e, face_f);
+  rc = build_connectivity(m, X, nbr, nbr_fo, face_e, face_f);
   if (rc) { free_mesh(m); return rc; }
   m->nfaces = (long long)face_e.size();
+  X.clear();
+  X.shrink_to_fit();
 
-  const long long E = m->E, NP = m->np, NF = m->nf;
-  rc = 0;
   rc |= dalloc(&m->d_ops, 1);
-  rc |= dalloc(&m->x, E * 3 * NP);
   rc |= dalloc(&m->geo, E * 10 * NP);
   rc |= dalloc(&m->acc, E * 3 * NP);
   rc |= dalloc(&m->xg, E * 3 * NP);
@@ -367,13 +409,6 @@ extern "C" int dg_mesh_create(const dg_mesh_desc* desc, dg_mesh** out) {
     free_mesh(m);
     return fail(DG_ENOMEM, "cudaMallocHost failed");
   }
-  double* d_layers = nullptr;
-  double* d_xi = nullptr;
-  if (dalloc(&d_layers, layers.size()) || dalloc(&d_xi, MAXN)) {
-    if (d_layers) cudaFree(d_layers);
-    free_mesh(m);
-    return DG_ENOMEM;
-  }
   cudaError_t err = cudaSuccess;
   err = cudaMemcpy(m->d_ops, &m->ops, sizeof(Ops), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(m->nbr, nbr.data(), sizeof(int32_t) * nbr.size(), cudaMemcpyHostToDevice);
@@ -382,25 +417,12 @@ extern "C" int dg_mesh_create(const dg_mesh_desc* desc, dg_mesh** out) {
     err = cudaMemcpy(m->face_e, face_e.data(), sizeof(int32_t) * face_e.size(), cudaMemcpyHostToDevice);
   if (err == cudaSuccess && m->nfaces)
     err = cudaMemcpy(m->face_f, face_f.data(), sizeof(int32_t) * face_f.size(), cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) err = cudaMemcpy(d_layers, layers.data(), sizeof(double) * layers.size(), cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) err = cudaMemcpy(d_xi, m->ops.xi, sizeof(double) * MAXN, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
-    cudaFree(d_layers);
-    cudaFree(d_xi);
     free_mesh(m);
     return fail(DG_ECUDA, std::string("dg_mesh_create upload: ") + cudaGetErrorString(err));
   }
-  MapParams mpd = mp;
-  mpd.r_layers = d_layers;
-  const long long work = E * NP;
-  k_nodes<<<(unsigned)((work + 255) / 256), 256>>>(mpd, E, m->n, d_xi, m->x);
-  err = cudaGetLastError();
-  if (err == cudaSuccess) {
-    rc = drv_geometry(m, 0);
-    if (rc == DG_OK) err = cudaDeviceSynchronize();
-  }
-  cudaFree(d_layers);
-  cudaFree(d_xi);
+  rc = drv_geometry(m, 0);
+  if (rc == DG_OK) err = cudaDeviceSynchronize();
   if (rc != DG_OK || err != cudaSuccess) {
     free_mesh(m);
     return rc ? rc : fail(DG_ECUDA, std::string("dg_mesh_create kernels: ") + cudaGetErrorString(err));

@@ -56,7 +56,7 @@ def lib():
     L = ctypes.CDLL(LIB_PATH)
     vp, dp, i32, i64p, d = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_double
     L.dg_last_error.restype = ctypes.c_char_p
-    L.dg_mesh_create.argtypes = [ctypes.POINTER(DgMeshDesc), ctypes.POINTER(vp)]
+    L.dg_mesh_create.argtypes = [ctypes.POINTER(DgMeshDesc), vp, ctypes.POINTER(vp)]
     L.dg_mesh_destroy.argtypes = [vp]
     L.dg_mesh_destroy.restype = None
     L.dg_mesh_sizes.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_int32), i64p]
@@ -113,11 +113,21 @@ def _ptr(t, shape=None, name="tensor"):
 class Mesh:
     """A library mesh: geometry, connectivity and workspace on the current CUDA device."""
 
-    def __init__(self, desc: W.MeshDesc):
+    def __init__(self, desc: W.MeshDesc, nodes=None):
+        """nodes: optional numpy array [n_elem][3][n_p] of node coordinates (the mesh as input);
+        None lets the library generate the workload mesh from desc."""
+        import numpy as np
         self.desc = desc
         self._c = to_c_desc(desc)
         h = ctypes.c_void_p()
-        _check(lib().dg_mesh_create(ctypes.byref(self._c), ctypes.byref(h)))
+        nptr = None
+        if nodes is not None:
+            self._nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+            if self._nodes.shape != (desc.n_elem, 3, desc.n_p):
+                raise DgError(f"nodes has shape {self._nodes.shape}, expected {(desc.n_elem, 3, desc.n_p)}")
+            nptr = ctypes.c_void_p(self._nodes.ctypes.data)
+        _check(lib().dg_mesh_create(ctypes.byref(self._c), nptr, ctypes.byref(h)))
+        self._nodes = None
         self._h = h
         ne, npe, nd = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
         _check(lib().dg_mesh_sizes(h, ctypes.byref(ne), ctypes.byref(npe), ctypes.byref(nd)))

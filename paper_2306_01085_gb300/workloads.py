@@ -183,6 +183,101 @@ CONFIGS = {
 }
 
 
+
+# ----------------------------------------------------------------------------------------------
+# workload meshes (node coordinates of the isoparametric elements)
+# ----------------------------------------------------------------------------------------------
+PANELS = [
+    ((1, 0, 0), (0, 1, 0), (0, 0, 1)),
+    ((0, 1, 0), (-1, 0, 0), (0, 0, 1)),
+    ((-1, 0, 0), (0, -1, 0), (0, 0, 1)),
+    ((0, -1, 0), (1, 0, 0), (0, 0, 1)),
+    ((0, 0, 1), (0, 1, 0), (-1, 0, 0)),
+    ((0, 0, -1), (0, 1, 0), (1, 0, 0)),
+]
+
+
+def gll_points(n):
+    """Gauss-Lobatto-Legendre points: -1, the roots of P'_{n-1}, +1 (where the nodes sit)."""
+    c = np.zeros(n)
+    c[n - 1] = 1.0
+    inner = np.polynomial.legendre.legroots(np.polynomial.legendre.legder(c)) if n > 2 else np.array([])
+    return np.concatenate([[-1.0], np.sort(np.real(inner)), [1.0]])
+
+
+def radial_layers(r_in, r_out, nz, h_first):
+    """Layer interfaces r_0 = r_in < ... < r_nz = r_out with heights h_first q^k (Sec. 3.3).
+
+    The growth ratio q solves sum_{k<nz} h_first q^k = r_out - r_in (bisection); h_first <= 0 gives
+    uniform layers.
+    """
+    total = r_out - r_in
+    if h_first <= 0.0 or nz == 1:
+        return r_in + total * np.arange(nz + 1) / nz
+    def excess(q):
+        return h_first * sum(q ** k for k in range(nz)) - total
+    lo, hi = 1.0, 2.0
+    if excess(lo) > 0:
+        lo, hi = 1e-6, 1.0
+    while excess(hi) < 0:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if excess(mid) > 0:
+            hi = mid
+        else:
+            lo = mid
+    q = 0.5 * (lo + hi)
+    r = r_in + np.concatenate([[0.0], np.cumsum(h_first * q ** np.arange(nz))])
+    r[-1] = r_out
+    return r
+
+
+def mesh_nodes(desc):
+    """GLL node positions X[e, d, i] of every element of the workload mesh (Sec. 3.3).
+
+    box   element e = i + nx (j + ny k); nodes at x = (i + (1 + xi_a)/2) lx/nx, ...
+    shell element e = k + nz (i + n (j + n P)) for panel P, angular cell (i, j), radial layer k;
+          equiangular gnomonic panels: direction c_P + tan(alpha) a_P + tan(beta) b_P,
+          normalised, alpha, beta in [-pi/4, pi/4], radius from the geometric layers.
+    node  i = a + n b + n^2 c (a along xi_1, the fastest), n = p + 1, at the GLL points.
+    """
+    n = desc.p + 1
+    xi = gll_points(n)
+    c3, b3, a3 = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ref = np.stack([xi[a3.ravel()], xi[b3.ravel()], xi[c3.ravel()]], axis=1)   # (n^3, 3)
+    s = 0.5 * (1.0 + ref)              # in [0, 1]
+    if desc.kind == 0:
+        hx, hy, hz = desc.lx / desc.nx, desc.ly / desc.ny, desc.lz / desc.nz
+        X = np.zeros((desc.n_elem, 3, n ** 3))
+        for k in range(desc.nz):
+            for j in range(desc.ny):
+                for i in range(desc.nx):
+                    e = i + desc.nx * (j + desc.ny * k)
+                    X[e, 0] = (i + s[:, 0]) * hx
+                    X[e, 1] = (j + s[:, 1]) * hy
+                    X[e, 2] = (k + s[:, 2]) * hz
+        return X
+    nn, nz = desc.nx, desc.nz
+    rl = radial_layers(desc.r_inner, desc.r_outer, nz, desc.h_first)
+    d_ang = 0.5 * math.pi / nn
+    X = np.zeros((desc.n_elem, 3, n ** 3))
+    for P, (c, a, b) in enumerate(PANELS):
+        c, a, b = np.array(c, float), np.array(a, float), np.array(b, float)
+        for j in range(nn):
+            for i in range(nn):
+                alpha = -0.25 * math.pi + (i + s[:, 0]) * d_ang
+                beta = -0.25 * math.pi + (j + s[:, 1]) * d_ang
+                dirv = c[:, None] + np.tan(alpha)[None, :] * a[:, None] + np.tan(beta)[None, :] * b[:, None]
+                dirv = dirv / np.sqrt((dirv ** 2).sum(0))[None, :]
+                for k in range(nz):
+                    e = k + nz * (i + nn * (j + nn * P))
+                    r = rl[k] + s[:, 2] * (rl[k + 1] - rl[k])
+                    X[e] = dirv * r[None, :]
+    return X
+
+
+
 # ----------------------------------------------------------------------------------------------
 # SplitMix64 counter-based random numbers
 # ----------------------------------------------------------------------------------------------
@@ -236,13 +331,25 @@ def _wavevectors(kmax=3):
 def fourier_field(seed: int, stream: int, xs: np.ndarray, kmax=3) -> np.ndarray:
     """Random Fourier sum over integer wavevectors 0 < |k|_2 <= kmax at points xs[..., 3].
 
-    f(x) = sum_k a_k cos(2 pi k.x) + b_k sin(2 pi k.x), a, b ~ U(-1, 1), divided by
-    sum_k (|a_k| + |b_k|) so that |f| <= 1 everywhere. Periodic on the unit cube.
+    f(x) = sum_k a_k cos(2 pi k.x) + b_k sin(2 pi k.x), a, b ~ U(-1, 1), divided by its maximum
+    modulus on the 32^3 lattice of one period (the unit cube), so the field has amplitude 1
+    independently of the mesh. Periodic on the unit cube.
     """
     ks = _wavevectors(kmax)
     nk = ks.shape[0]
     ab = 2.0 * uniform01(seed, 2 * nk, offset=stream * 4096) - 1.0
     a, b = ab[:nk], ab[nk:]
+    return _fourier_sum(ks, a, b, xs, kmax) / _fourier_max(ks, a, b, kmax)
+
+
+def _fourier_max(ks, a, b, kmax, m=32):
+    g = np.arange(m) / m
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    return float(np.abs(_fourier_sum(ks, a, b, lat, kmax)).max())
+
+
+def _fourier_sum(ks, a, b, xs, kmax):
+    nk = ks.shape[0]
     # exp(2 pi i k.x) as a product of per-axis powers of exp(2 pi i x_d)
     flat = xs.reshape(-1, 3)
     base = [np.exp(2j * np.pi * flat[:, d]) for d in range(3)]
@@ -258,8 +365,7 @@ def fourier_field(seed: int, stream: int, xs: np.ndarray, kmax=3) -> np.ndarray:
         k0, k1, k2 = (int(c) for c in ks[k])
         z = pw[0][k0] * pw[1][k1] * pw[2][k2]
         f += a[k] * z.real + b[k] * z.imag
-    f = f.reshape(xs.shape[:-1])
-    return f / (np.abs(a).sum() + np.abs(b).sum())
+    return f.reshape(xs.shape[:-1])
 
 
 # ----------------------------------------------------------------------------------------------

@@ -81,7 +81,7 @@ def test_shell_matching_and_boundaries():
 
 def test_radial_layers_geometric_growth():
     d = W.shell_desc(n=2, nr=8, p=2)
-    r = OM.radial_layers(d.r_inner, d.r_outer, d.nz, d.h_first)
+    r = W.radial_layers(d.r_inner, d.r_outer, d.nz, d.h_first)
     h = np.diff(r)
     assert abs(h[0] - d.h_first) < 1e-12 * d.r_outer
     assert abs(r[-1] - d.r_outer) < 1e-12 and np.allclose(h[1:] / h[:-1], h[1] / h[0], rtol=1e-9)
