@@ -136,6 +136,24 @@ int dg_jvp(dg_mesh* mesh, const double* u, const double* v, double t, int32_t mo
 int dg_mass_apply(dg_mesh* mesh, const double* v, double* mv, void* stream);
 
 /*
+ * The residual of dg_residual (q computed from u) for callers that must not have the library
+ * allocate device memory during the call: applications whose own caching allocator has reserved
+ * the device's memory, or loops that cannot absorb the device synchronisation that cudaMalloc and
+ * cudaFree may cause. The paper has no counterpart; this is a deployment variant.
+ * The call allocates nothing: its scratch is one 16 MiB FP64 array in the library's device image
+ * (a file-scope __device__ array that every GPU loading the library holds until process exit).
+ * A mesh needs n_elem (20 n_p + 150 (p+1)^2) doubles of it, so at most 1,109 elements at p = 2,
+ * 569 at p = 3 and 335 at p = 4; larger meshes are rejected with DG_EINVAL and a message giving
+ * both sizes. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. All calls share the one array and every call
+ * overwrites what it reads before reading it, so nothing needs clearing between calls; calls that
+ * overlap on the GPU (other streams, other threads) race on the array and must be serialised by
+ * the caller. The mesh itself (geometry, connectivity) is allocated by dg_mesh_create as usual.
+ */
+int dg_residual_static(dg_mesh* mesh, const double* u, double t, double* r, void* stream);
+
+/*
  * Tracing. dg_profile_start makes every kernel the library launches for this mesh record a pair
  * of CUDA events on the stream it runs on (capacity = most launches recorded; launches beyond it
  * are counted, not timed). dg_profile_stop synchronises those events, accumulates the device time
