@@ -29,7 +29,6 @@ sys.path.insert(0, ROOT)
 METRIC = "DG residual+Jv DOFs/s"
 UNIT = "DOF/s"
 CONFIG_NAME = "shell16x8_p4"
-FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64 (profiling recipe nominal table)
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -148,29 +147,14 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------------------------
-# algorithmic FP64 work of the kernels (per element, per launch), see the design doc
+# FP64 work of the kernels: (2 DFMA + DMUL + DADD) per element from one ncu capture of each kernel
+# (profiles/fp64_residual_jv_shell16x8_p4.md); only valid for the kernels of that capture, so the
+# table is keyed by the source digest of the library it was measured on.
 # ----------------------------------------------------------------------------------------------
-def fp64_flops_per_element(kernel, n, tangent=True):
-    """FP64 flops per element of one kernel launch counted from the algorithm (FMA = 2 flops).
-
-    Contractions are counted exactly; the pointwise flux/source/EUV part uses the per-point FP64
-    operation counts stated in the design doc (value + tangent with dual numbers)."""
-    NP, NF = n ** 3, n * n
-    C = 10 if tangent else 5
-    if kernel == "k_volume":
-        proj = 3 * C * 3 * 2                       # Fref_a = sum_d G_ad F_cd (value + tangent)
-        weak = 3 * C * n * 2                       # sum_a D_a^T Fref_a
-        lift = 6 * C * 2
-        bt = 3 * C * n * 2                         # B^T along three directions
-        point = 560 if tangent else 250            # pointwise flux + source per Gauss point
-        return NP * (proj + weak + lift + bt + point)
-    if kernel == "k_grad":
-        return NP * C * (9 + 3 * 3 * n * 2 + 6 * 3 * 2 + 3) + 6 * NF * C
-    if kernel == "k_faces":
-        return 3 * NF * (2 * (520 if tangent else 230) + 120)
-    if kernel == "k_interp":
-        return NP * C * 3 * n * 2 + 6 * NF * C * n * 2
-    return 0
+FP64_FLOPS_PER_ELEMENT = {("k_grad", 5): 247981.3, ("k_volume", 5): 205500.0, ("k_faces", 5): 84125.0}
+DRAM_BYTES_PER_LAUNCH = {("k_grad", 5): 1206637056.0, ("k_volume", 5): 912731136.0, ("k_faces", 5): 755406848.0}
+# FP64 peak from unit counts: 2 DFMA lanes/SM/cycle x 152 SMs x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
 
 def main_ours(args):
@@ -244,14 +228,17 @@ def main_ours(args):
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_cnt) = dom
     per_launch_ms = dom_ms / dom_cnt
-    flops = fp64_flops_per_element(dom_name, desc.p + 1) * mesh.n_elem
+    key = (dom_name, desc.p + 1)
+    flops = FP64_FLOPS_PER_ELEMENT.get(key, float("nan")) * mesh.n_elem
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     probe = DG.probe_fp64()
-    roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4), "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
-                "peak_kind": "FP64 nominal of the profiling recipe", "peak_probe": round(probe, 4),
-                "launch_ms": round(per_launch_ms, 4), "fp64_flops_per_launch": flops,
-                "share": round(dom_ms / sum(v[0] for v in prof.values()), 4)}
+    traffic = DRAM_BYTES_PER_LAUNCH.get(key) if args.config == CONFIG_NAME else None
+    roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "peak_kind": "FP64 from unit counts x max SM clock (2 DFMA/SM/cycle, 152 SMs, 2.07 GHz)",
+                "peak_probe": round(probe, 4), "launch_ms": round(per_launch_ms, 4), "fp64_flops_per_launch": flops,
+                "share": round(dom_ms / sum(v[0] for v in prof.values()), 4),
+                "dram_gbs": round(traffic / (per_launch_ms * 1e-3) / 1e9, 1) if traffic else None}
 
     # end to end through the public API: pinned host in, host out, every step
     e2e = None
