@@ -153,6 +153,7 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------------
 FP64_FLOPS_PER_ELEMENT = {("k_grad", 5): 247981.3, ("k_volume", 5): 205500.0, ("k_faces", 5): 84125.0}
 DRAM_BYTES_PER_LAUNCH = {("k_grad", 5): 1206637056.0, ("k_volume", 5): 912731136.0, ("k_faces", 5): 755406848.0}
+CAPTURE_DIGEST = "ba3430f89bcfb9b533d92c861ce8c397f31d3b7678f5f17fb0398a47cc7d1150"   # build digest of the library these counters were taken on
 # FP64 peak from unit counts: 2 DFMA lanes/SM/cycle x 152 SMs x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
@@ -232,12 +233,14 @@ def main_ours(args):
     flops = FP64_FLOPS_PER_ELEMENT.get(key, float("nan")) * mesh.n_elem
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     probe = DG.probe_fp64()
-    traffic = DRAM_BYTES_PER_LAUNCH.get(key) if args.config == CONFIG_NAME else None
+    fresh = B._digest() == CAPTURE_DIGEST
+    traffic = DRAM_BYTES_PER_LAUNCH.get(key) if (args.config == CONFIG_NAME and fresh) else None
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "peak_kind": "FP64 from unit counts x max SM clock (2 DFMA/SM/cycle, 152 SMs, 2.07 GHz)",
                 "peak_probe": round(probe, 4), "launch_ms": round(per_launch_ms, 4), "fp64_flops_per_launch": flops,
                 "share": round(dom_ms / sum(v[0] for v in prof.values()), 4),
+                "counters": "ncu capture of this build" if fresh else "ncu capture of an earlier build (flops as then)",
                 "dram_gbs": round(traffic / (per_launch_ms * 1e-3) / 1e9, 1) if traffic else None}
 
     # end to end through the public API: pinned host in, host out, every step
