@@ -153,6 +153,83 @@ int dg_mass_apply(dg_mesh* mesh, const double* v, double* mv, void* stream);
  */
 int dg_residual_static(dg_mesh* mesh, const double* u, double t, double* r, void* stream);
 
+/* ----------------------------------------------------------------------------------------------
+ * Implicit time step (Sec. 3.1-3.2): DIRK stages solved by Newton-GMRES
+ * -------------------------------------------------------------------------------------------- */
+#define DG_PC_NONE 0         /* no preconditioner */
+#define DG_PC_BJ   1         /* exact element diagonal blocks of J_G, FP32 LU (block-Jacobi) */
+#define DG_PC_MLP  2         /* learned diagonal + low-rank inverse per element */
+
+#define DG_REFRESH_STEP   0  /* build the preconditioner once per step, at u_n */
+#define DG_REFRESH_STAGE  1  /* rebuild at the start of every stage */
+#define DG_REFRESH_NEWTON 2  /* rebuild at every Newton iteration */
+
+#define DG_STATS_HIST 64
+
+typedef struct dg_solver_opts {
+    int32_t stages;          /* DIRK stages: 1 (backward Euler), 2 (DIRK(2,2)), 3 (DIRK(3,3)) */
+    int32_t gmres_restart;   /* Krylov basis size before restart, 1..63 (30) */
+    int32_t max_restarts;    /* GMRES cycles per Newton system before DG_ENOTCONV (10) */
+    int32_t max_newton;      /* Newton iterations per stage before DG_ENOTCONV (20) */
+    int32_t precond;         /* DG_PC_* */
+    int32_t precond_refresh; /* DG_REFRESH_* */
+    int32_t jv_mode;         /* DG_JV_EXACT or DG_JV_FD for the GMRES operator */
+    int32_t reserved;
+    double newton_rtol;      /* stop when ||G||_2 <= newton_rtol ||G(U^0)||_2 (1e-8) */
+    double gmres_rtol;       /* each Newton system to ||b - J x|| <= gmres_rtol ||b|| (1e-3) */
+    double abs_floor;        /* or when ||G||_2 <= abs_floor ||M U||_2 (1e-14) */
+} dg_solver_opts;
+
+typedef struct dg_step_stats {
+    int32_t status;                 /* the call's return code */
+    int32_t newton_iters[3];        /* Newton iterations per stage */
+    int32_t gmres_iters[3];         /* GMRES iterations per stage (all Newton systems) */
+    int32_t n_hist;                 /* entries of res_hist */
+    double res_hist[DG_STATS_HIST]; /* ||G||_2 at every Newton iterate, stage after stage */
+    double wall_ms;                 /* host wall time of the call */
+    double precond_ms;              /* of which building preconditioners */
+} dg_step_stats;
+
+/* Defaults: 3 stages, GMRES(30), 10 cycles, 20 Newton iterations, no preconditioner, exact Jv,
+ * Newton 1e-8 relative, GMRES 1e-3 relative, floor 1e-14. */
+void dg_solver_opts_default(dg_solver_opts* opts);
+
+/* The DIRK tableau the step uses, derived from the order conditions: a [stages][stages] row-major,
+ * c [stages]. */
+int dg_dirk_tableau(int32_t stages, double* a, double* c);
+
+/*
+ * One DIRK step u_n -> u_{n+1} in place on u (device, [n_elem][5][n_p]) for M du/dt = r(u), Sec.
+ * 3.1: stage i solves G(U) = M (U - u_n) - dt sum_{j<i} a_ij r(U_j) - dt a_ii r(U) = 0 by Newton's
+ * method (Eq. NewtonSolve) from the previous stage value; every Newton system J_G dU = -G,
+ * J_G = M - dt a_ii J_r, is solved by right-preconditioned restarted GMRES with FP64 Arnoldi
+ * (classical Gram-Schmidt applied twice) and FP64 least squares. Synchronises the stream (the host
+ * reads norms and Hessenberg columns). stats may be NULL. Errors: DG_ENOTCONV (Newton or GMRES
+ * limits), DG_ENAN (non-finite norm or a zero block pivot), DG_EINVAL, DG_ENOMEM, DG_ECUDA. On an
+ * error u is left unchanged; the caller may retry with a smaller dt.
+ */
+int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, const dg_solver_opts* opts,
+                     dg_step_stats* stats, void* stream);
+
+/*
+ * Build a preconditioner of J_G = M - dt_aii J_r(u) at state u and time t.
+ * DG_PC_BJ: the exact diagonal block of every element (including the path through the
+ * neighbours' LDG gradients) is computed column by column by block-diagonal tangent sweeps, then
+ * factored by FP32 LU with partial pivoting. Synchronises the stream. DG_ENAN on a zero pivot.
+ * The blocks are exact when no two faces of an element border the same neighbour (every shell;
+ * boxes with at least 3 elements along each periodic direction); otherwise the gradient lifted
+ * from one shared face into the other is left out and the block is an approximation.
+ */
+int dg_precond_setup(dg_mesh* mesh, int32_t kind, const double* u, double t, double dt_aii, void* stream);
+
+/* y = P^{-1} x with the preconditioner last built (x, y FP64 [n_elem][5][n_p]; may alias). */
+int dg_precond_apply(dg_mesh* mesh, int32_t kind, const double* x, double* y, void* stream);
+
+/* Assemble the exact diagonal blocks of J_G = M - dt_aii J_r(u) (the ones DG_PC_BJ factors) into a
+ * caller device buffer out, FP32 [n_elem][5 n_p][5 n_p], each block column-major (out[e][j][i] =
+ * row i, column j; rows and columns in the element's [var][node] order). Stream-ordered. */
+int dg_block_assemble(dg_mesh* mesh, const double* u, double t, double dt_aii, float* out, void* stream);
+
 /*
  * Tracing. dg_profile_start makes every kernel the library launches for this mesh record a pair
  * of CUDA events on the stream it runs on (capacity = most launches recorded; launches beyond it

@@ -64,6 +64,7 @@ struct Workspace {
   double* qg = nullptr;   // [2][E][3][5][Np] Gauss values of q
   double* qf = nullptr;   // [2][E][6][15][Nf] face traces of q
   double* fh = nullptr;   // [2][E][6][5][Nf] F_hat . (w n dS) per element face
+  double* qx = nullptr;   // [E][6][15][Nf] cross gradient traces (block-diagonal tangent only)
   double* tmp = nullptr;  // [2][n_dof] scratch vectors (FD Jv, nodal q)
   double* red = nullptr;  // [1024] reduction partials
   double* red_host = nullptr;  // pinned host copy
@@ -73,8 +74,9 @@ struct Workspace {
 
 namespace dg {
 enum KernelKind {
-  KK_INTERP = 0, KK_GRAD, KK_FACES, KK_VOLUME, KK_TENSOR, KK_BLAS, KK_GEOMETRY, KK_COUNT
+  KK_INTERP = 0, KK_GRAD, KK_FACES, KK_VOLUME, KK_TENSOR, KK_BLAS, KK_GEOMETRY, KK_LU, KK_PRECOND, KK_COUNT
 };
+struct Solver;
 struct Prof {
   bool on = false;
   int cap = 0, used = 0;
@@ -103,7 +105,10 @@ struct dg_mesh {
   int32_t* face_e = nullptr; // [F] owner element of each face visited once by the face kernel
   int32_t* face_f = nullptr; // [F] owner local face
   dg::Workspace ws;
+  dg::Solver* solver = nullptr;   // implicit-step storage, created on first use
 };
+
+void dg_solver_release(dg_mesh* m);
 
 namespace dg {
 
@@ -136,6 +141,8 @@ struct Driver {
   static int q_to_nodal(dg_mesh* m, double* q, cudaStream_t s);
   static int q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s);
   static int mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
+  // J_r probe restricted to each element's own diagonal block (exact, one column per element)
+  static int jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s);
 };
 
 // orientation map of face point (is, it) to the neighbour's face point index

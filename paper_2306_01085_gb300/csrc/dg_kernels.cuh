@@ -171,11 +171,16 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
 // --------------------------------------------------------------------------------------------
 // k_grad: LDG gradient in Gauss space (Eq. DGformulation a) and its face traces
 // --------------------------------------------------------------------------------------------
-template <int N, int NC>
+// BLK (block-diagonal tangent, NC = 2): the tangent keeps only the element's own perturbation
+// (u_hat picks up half of the own trace on interior faces) and qx receives, per face, the trace of
+// the gradient tangent this element would get from its neighbour's perturbation across that face:
+// kappa(f) (w n dS)(f) u_dot_nb(f) / 2 with kappa(f) = sum_k e_face[k]^2 / (w |J|)(g(f, k)).
+template <int N, int NC, bool BLK>
 __global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const double* __restrict__ geo,
                        const double* __restrict__ fgeo, const int* __restrict__ nbr,
                        const int* __restrict__ nbr_fo, const double* __restrict__ ug,
-                       const double* __restrict__ uf, double* __restrict__ qg, double* __restrict__ qf) {
+                       const double* __restrict__ uf, double* __restrict__ qg, double* __restrict__ qf,
+                       double* __restrict__ qx) {
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
   __shared__ SmemOps so;
   extern __shared__ double smem[];
@@ -211,8 +216,27 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const d
       const long long nbase = (long long)nb * 30 * NF + (fo & 7) * 5 * NF + f2;
       for (int pl = 0; pl < NC; ++pl)
         for (int c = 0; c < 5; ++c) oth[5 * pl + c] = uf[pl * plane_f + nbase + c * NF];
-      for (int c = 0; c < C; ++c) dst[c * NF] = 0.5 * (own[c] + oth[c]);
+      if constexpr (BLK) {
+        for (int c = 0; c < 5; ++c) {
+          dst[c * NF] = 0.5 * (own[c] + oth[c]);
+          dst[(5 + c) * NF] = 0.5 * own[5 + c];
+        }
+        const double* ev = (phi & 1) ? so.eR : so.eL;
+        double kappa = 0.0;
+        for (int k = 0; k < N; ++k) kappa += ev[k] * ev[k] / geo[e * 10 * NP + 9 * NP + face_vol_point<N>(phi, f, k)];
+        double* xo = qx + (e * 6 + phi) * 15 * NF + f;
+        for (int d = 0; d < 3; ++d) {
+          const double kn = 0.5 * kappa * fgeo[((e * 6 + phi) * 4 + d) * NF + f];
+          for (int c = 0; c < 5; ++c) xo[(d * 5 + c) * NF] = kn * oth[5 + c];
+        }
+      } else {
+        for (int c = 0; c < C; ++c) dst[c * NF] = 0.5 * (own[c] + oth[c]);
+      }
     } else if (nb == -DG_BC_WALL) {
+      if constexpr (BLK) {
+        double* xo = qx + (e * 6 + phi) * 15 * NF + f;
+        for (int k = 0; k < 15; ++k) xo[k * NF] = 0.0;
+      }
       const double sr = exp(0.5 * own[0]);
       dst[0] = own[0];
       dst[NF] = 0.0;
@@ -227,6 +251,10 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const d
         dst[9 * NF] = 0.5 * sr * P.t_wall * own[5];
       }
     } else {
+      if constexpr (BLK) {
+        double* xo = qx + (e * 6 + phi) * 15 * NF + f;
+        for (int k = 0; k < 15; ++k) xo[k * NF] = 0.0;
+      }
       for (int c = 0; c < C; ++c) dst[c * NF] = own[c];
     }
   }
@@ -309,12 +337,30 @@ __device__ __forceinline__ void st<Dual>(double* p, long long plane, Dual v) {
   p[plane] = v.d;
 }
 
-template <int N, int NC>
+// interior numerical flux of Eq. LDG2 with the normal n = w n dS of the first side:
+// F_hat . n = (F(u, q) + F(u2, q2)) . n / 2 + sigma(u_hat) (u - u_hat) |n|, u_hat = (u + u2) / 2
+template <typename S>
+__device__ __forceinline__ void face_flux_interior(const Phys& P, const S u[5], const S q[3][5], const S u2[5],
+                                                   const S q2[3][5], const double n[3], double area, S out[5]) {
+  S f1[5], fn[5], uh[5], sg[5];
+  flux_dot_n(P, u, q, n, true, f1);
+  flux_dot_n(P, u2, q2, n, true, fn);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) uh[c] = 0.5 * (u[c] + u2[c]);
+  sigma_diag(P, uh, sg);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) out[c] = 0.5 * (f1[c] + fn[c]) + sg[c] * ((0.5 * area) * (u[c] - u2[c]));
+}
+
+// BLK (NC = 2): interior faces evaluate the tangent twice, once for each side's diagonal block:
+// the own side carries its perturbation and the other side only the gradient it receives from it
+// across this face (qx of the other element).
+template <int N, int NC, bool BLK>
 __global__ void k_faces(long long E, long long F, Phys P, const int* __restrict__ face_e,
                         const int* __restrict__ face_f, const int* __restrict__ nbr,
                         const int* __restrict__ nbr_fo, const double* __restrict__ fgeo,
                         const double* __restrict__ uf, const double* __restrict__ qf,
-                        double* __restrict__ fh) {
+                        const double* __restrict__ qx, double* __restrict__ fh) {
   using S = typename std::conditional<NC == 2, Dual, double>::type;
   constexpr int NF = Shape<N>::NF;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -351,17 +397,33 @@ __global__ void k_faces(long long E, long long F, Phys P, const int* __restrict_
     for (int d = 0; d < 3; ++d)
 #pragma unroll
       for (int c = 0; c < 5; ++c) q2[d][c] = ld<S, NC>(qf + qb2 + (d * 5 + c) * NF, plane_q);
-    S f1[5], fn[5], uh[5], sg[5];
-    flux_dot_n(P, u, q, n, true, f1);
-    flux_dot_n(P, u2, q2, n, true, fn);
-#pragma unroll
-    for (int c = 0; c < 5; ++c) uh[c] = 0.5 * (u[c] + u2[c]);
-    sigma_diag(P, uh, sg);
-#pragma unroll
-    for (int c = 0; c < 5; ++c) out[c] = 0.5 * (f1[c] + fn[c]) + sg[c] * ((0.5 * area) * (u[c] - u2[c]));
     const long long ob2 = (long long)nb * 30 * NF + phi2 * 5 * NF + f2;
+    if constexpr (BLK) {
+      // block of the own element: the neighbour side carries only the cross gradient tangent
+      S ua[5], qa[3][5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) st<S>(fh + ob2 + c * NF, plane_u, -out[c]);
+      for (int c = 0; c < 5; ++c) ua[c] = Dual{u2[c].v, 0.0};
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) qa[d][c] = Dual{q2[d][c].v, qx[((long long)nb * 6 + phi2) * 15 * NF + (d * 5 + c) * NF + f2]};
+      face_flux_interior(P, u, q, ua, qa, n, area, out);
+      // block of the neighbour: the own side carries only its cross gradient tangent
+      S ub[5], qb[3][5], outb[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) ub[c] = Dual{u[c].v, 0.0};
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) qb[d][c] = Dual{q[d][c].v, qx[(e * 6 + phi) * 15 * NF + (d * 5 + c) * NF + f]};
+      face_flux_interior(P, ub, qb, u2, q2, n, area, outb);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) st<S>(fh + ob2 + c * NF, plane_u, -outb[c]);
+    } else {
+      face_flux_interior(P, u, q, u2, q2, n, area, out);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) st<S>(fh + ob2 + c * NF, plane_u, -out[c]);
+    }
   } else if (nb == -DG_BC_WALL) {
     S ubd[5], sg[5];
     wall_trace(P, u, ubd);
@@ -740,30 +802,30 @@ static int run_interp(dg_mesh* m, const double* u, const double* v, cudaStream_t
   return DG_OK;
 }
 
-template <int N, int NC>
+template <int N, int NC, bool BLK = false>
 static int run_grad(dg_mesh* m, cudaStream_t s) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
   const size_t sm = Smem<N, NC>::grad;
-  int rc = set_smem(k_grad<N, NC>, sm);
+  int rc = set_smem(k_grad<N, NC, BLK>, sm);
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
   prof_begin(m, s, KK_GRAD);
-  k_grad<N, NC><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, m->phys, m->geo, m->fgeo, m->nbr, m->nbr_fo,
-                                              m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf);
+  k_grad<N, NC, BLK><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, m->phys, m->geo, m->fgeo, m->nbr, m->nbr_fo,
+                                                   m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf, m->ws.qx);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_grad");
   return DG_OK;
 }
 
-template <int N, int NC>
+template <int N, int NC, bool BLK = false>
 static int run_faces(dg_mesh* m, cudaStream_t s) {
   constexpr int NF = Shape<N>::NF;
   const long long work = m->nfaces * NF;
   const int threads = 128;
   const unsigned blocks = (unsigned)((work + threads - 1) / threads);
   prof_begin(m, s, KK_FACES);
-  k_faces<N, NC><<<blocks, threads, 0, s>>>(m->E, m->nfaces, m->phys, m->face_e, m->face_f, m->nbr, m->nbr_fo,
-                                             m->fgeo, m->ws.uf, m->ws.qf, m->ws.fh);
+  k_faces<N, NC, BLK><<<blocks, threads, 0, s>>>(m->E, m->nfaces, m->phys, m->face_e, m->face_f, m->nbr,
+                                                  m->nbr_fo, m->fgeo, m->ws.uf, m->ws.qf, m->ws.qx, m->ws.fh);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_faces");
   return DG_OK;
@@ -815,6 +877,18 @@ int Driver<N>::residual(dg_mesh* m, const double* u, const double* v, double t, 
   int rc = tangent ? run_faces<N, 2>(m, s) : run_faces<N, 1>(m, s);
   if (rc) return rc;
   return tangent ? run_volume<N, 2>(m, t, r, jv, s) : run_volume<N, 1>(m, t, r, nullptr, s);
+}
+
+template <int N>
+int Driver<N>::jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv,
+                            cudaStream_t s) {
+  int rc = run_interp<N, 2>(m, u, probe, s);
+  if (rc) return rc;
+  rc = run_grad<N, 2, true>(m, s);
+  if (rc) return rc;
+  rc = run_faces<N, 2, true>(m, s);
+  if (rc) return rc;
+  return run_volume<N, 2>(m, t, nullptr, jv, s);
 }
 
 template <int N>

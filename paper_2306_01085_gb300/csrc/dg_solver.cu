@@ -1,0 +1,735 @@
+// Implicit DIRK step with Newton-GMRES (Sec. 3.1-3.2) and the block-Jacobi preconditioner.
+//
+// Stage i of the DIRK scheme (Alexander 1977) solves G(U) = M (U - u_n) - dt sum_{j<i} a_ij r(U_j)
+// - dt a_ii r(U) = 0 by Newton's method (Eq. NewtonSolve); each Newton system J_G dU = -G with
+// J_G = M - dt a_ii J_r is solved by right-preconditioned restarted GMRES whose only operator is
+// the Jacobian-vector product. Arnoldi (classical Gram-Schmidt applied twice), the Hessenberg
+// least-squares problem and every norm are FP64. The block-Jacobi preconditioner factors the exact
+// element diagonal blocks of J_G in FP32 (batched LU with partial pivoting).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dg_internal.cuh"
+
+namespace dg {
+
+// ------------------------------------------------------------------------------------------
+// DIRK tableaux from the order conditions (host)
+// ------------------------------------------------------------------------------------------
+// 2 stages: b = (1-g, g), c = (g, 1), order 2 requires g^2 - 2g + 1/2 = 0 -> g = 1 - 1/sqrt(2).
+// 3 stages: stiffly accurate (last row of A = b), equal diagonal g; unknowns g, a21, b1, b2 solve
+// b.1 = 1, b.c = 1/2, b.c^2 = 1/3, b.A.c = 1/6 (Newton's method from an L-stable starting point).
+static int dirk_tableau(int stages, double A[3][3], double c[3]) {
+  std::memset(A, 0, 9 * sizeof(double));
+  if (stages == 1) {
+    A[0][0] = 1.0;
+    c[0] = 1.0;
+    return DG_OK;
+  }
+  if (stages == 2) {
+    const double g = 1.0 - 1.0 / std::sqrt(2.0);
+    A[0][0] = g;
+    A[1][0] = 1.0 - g;
+    A[1][1] = g;
+    c[0] = g;
+    c[1] = 1.0;
+    return DG_OK;
+  }
+  if (stages != 3) return fail(DG_EINVAL, "DIRK stages must be 1, 2 or 3");
+  double x[4] = {0.44, 0.28, 1.2, -0.64};
+  auto cond = [](const double* y, double* f) {
+    const double g = y[0], a21 = y[1], b1 = y[2], b2 = y[3];
+    const double c1 = g, c2 = a21 + g, c3 = 1.0;
+    const double Ac[3] = {g * c1, a21 * c1 + g * c2, b1 * c1 + b2 * c2 + g * c3};
+    f[0] = b1 + b2 + g - 1.0;
+    f[1] = b1 * c1 + b2 * c2 + g * c3 - 0.5;
+    f[2] = b1 * c1 * c1 + b2 * c2 * c2 + g * c3 * c3 - 1.0 / 3.0;
+    f[3] = b1 * Ac[0] + b2 * Ac[1] + g * Ac[2] - 1.0 / 6.0;
+  };
+  for (int it = 0; it < 60; ++it) {
+    double f[4], J[4][5];
+    cond(x, f);
+    for (int k = 0; k < 4; ++k) {
+      double xp[4], xm[4], fp[4], fm[4];
+      std::memcpy(xp, x, sizeof(x));
+      std::memcpy(xm, x, sizeof(x));
+      xp[k] += 1e-7;
+      xm[k] -= 1e-7;
+      cond(xp, fp);
+      cond(xm, fm);
+      for (int r = 0; r < 4; ++r) J[r][k] = (fp[r] - fm[r]) / 2e-7;
+    }
+    for (int r = 0; r < 4; ++r) J[r][4] = -f[r];
+    for (int k = 0; k < 4; ++k) {  // Gaussian elimination with partial pivoting
+      int p = k;
+      for (int r = k + 1; r < 4; ++r)
+        if (std::fabs(J[r][k]) > std::fabs(J[p][k])) p = r;
+      for (int q = 0; q < 5; ++q) std::swap(J[k][q], J[p][q]);
+      for (int r = k + 1; r < 4; ++r) {
+        const double l = J[r][k] / J[k][k];
+        for (int q = k; q < 5; ++q) J[r][q] -= l * J[k][q];
+      }
+    }
+    double dx[4];
+    for (int k = 3; k >= 0; --k) {
+      double s = J[k][4];
+      for (int q = k + 1; q < 4; ++q) s -= J[k][q] * dx[q];
+      dx[k] = s / J[k][k];
+    }
+    double mx = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      x[k] += dx[k];
+      mx = std::fmax(mx, std::fabs(dx[k]));
+    }
+    if (mx < 1e-15) break;
+  }
+  const double g = x[0];
+  A[0][0] = g;
+  A[1][0] = x[1];
+  A[1][1] = g;
+  A[2][0] = x[2];
+  A[2][1] = x[3];
+  A[2][2] = g;
+  c[0] = g;
+  c[1] = x[1] + g;
+  c[2] = 1.0;
+  return DG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// vector kernels (FP64); reductions use a fixed grid and a fixed summation order
+// ------------------------------------------------------------------------------------------
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int MAXK = 64;          // largest restart + 1
+
+__global__ void k_lincomb(long long n, double a, const double* __restrict__ x, double b,
+                          const double* __restrict__ y, double c, const double* __restrict__ z,
+                          double* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = a * x[i];
+    if (y) v = fma(b, y[i], v);
+    if (z) v = fma(c, z[i], v);
+    out[i] = v;
+  }
+}
+
+// out = x * (*scale_num) / sqrt(*scale_den)  (device-resident scalars)
+__global__ void k_scale_dev(long long n, const double* __restrict__ x, const double* __restrict__ den,
+                            double* __restrict__ out) {
+  const double s = 1.0 / sqrt(*den);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = x[i] * s;
+}
+
+// partial[j][block] = sum_i V_j[i] w[i] for j < k; partial[k][block] = sum_i w[i]^2
+__global__ void k_mdot(long long n, int k, const double* __restrict__ V, long long ldv,
+                       const double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double red[RED_THREADS];
+  double acc[MAXK];
+#pragma unroll 1
+  for (int j = 0; j <= k; ++j) acc[j] = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+#pragma unroll 1
+    for (int j = 0; j < k; ++j) acc[j] = fma(V[j * ldv + i], wi, acc[j]);
+    acc[k] = fma(wi, wi, acc[k]);
+  }
+#pragma unroll 1
+  for (int j = 0; j <= k; ++j) {
+    red[threadIdx.x] = acc[j];
+    __syncthreads();
+    for (int st = RED_THREADS / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[j * RED_BLOCKS + blockIdx.x] = red[0];
+    __syncthreads();
+  }
+}
+
+// out[j] = sum_b partial[j][b] (+= into out when accumulate); also out_sq = partial[k] sum
+__global__ void k_mdot_finish(int k, const double* __restrict__ partial, double* __restrict__ out, int accumulate) {
+  const int j = threadIdx.x;
+  if (j > k) return;
+  double s = 0.0;
+  for (int b = 0; b < RED_BLOCKS; ++b) s += partial[j * RED_BLOCKS + b];
+  out[j] = accumulate ? out[j] + s : s;
+}
+
+// w -= sum_j h[j] V_j for j < k
+__global__ void k_maxpy(long long n, int k, const double* __restrict__ V, long long ldv,
+                        const double* __restrict__ h, double* __restrict__ w) {
+  __shared__ double hs[MAXK];
+  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = w[i];
+    for (int j = 0; j < k; ++j) v = fma(-hs[j], V[j * ldv + i], v);
+    w[i] = v;
+  }
+}
+
+// out = sum_j y[j] V_j (j < k)
+__global__ void k_combine(long long n, int k, const double* __restrict__ V, long long ldv,
+                          const double* __restrict__ y, double* __restrict__ out) {
+  __shared__ double ys[MAXK];
+  if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v = fma(ys[j], V[j * ldv + i], v);
+    out[i] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// block-Jacobi: probes, column scatter, FP32 batched LU (column-major blocks), solves
+// ------------------------------------------------------------------------------------------
+__global__ void k_probe(long long E, int n, int j, double* __restrict__ v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < E * n; i += (long long)gridDim.x * blockDim.x)
+    v[i] = ((int)(i % n) == j) ? 1.0 : 0.0;
+}
+
+// column j of every block: B[e][j][row] = mv[e][row] - c jv[e][row]
+__global__ void k_scatter_col(long long E, int n, int j, double c, const double* __restrict__ mv,
+                              const double* __restrict__ jv, float* __restrict__ blocks) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < E * n; i += (long long)gridDim.x * blockDim.x) {
+    const long long e = i / n;
+    const int row = (int)(i % n);
+    blocks[(e * n + j) * (long long)n + row] = (float)(mv[i] - c * jv[i]);
+  }
+}
+
+// in-place LU with partial pivoting of one n x n column-major block per CTA
+__global__ void k_lu(long long E, int n, float* __restrict__ blocks, int* __restrict__ piv, int* __restrict__ info) {
+  const long long e = blockIdx.x;
+  float* A = blocks + e * (long long)n * n;
+  int* pv = piv + e * n;
+  __shared__ float sval[256];
+  __shared__ int sidx[256];
+  __shared__ int p_sh;
+  for (int k = 0; k < n; ++k) {
+    float best = -1.0f;
+    int bi = k;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const float a = fabsf(A[(long long)k * n + i]);
+      if (a > best) { best = a; bi = i; }
+    }
+    sval[threadIdx.x] = best;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        const float o = sval[threadIdx.x + st];
+        const int oi = sidx[threadIdx.x + st];
+        if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+          sval[threadIdx.x] = o;
+          sidx[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      p_sh = sidx[0];
+      pv[k] = p_sh;
+      if (!(sval[0] > 0.0f)) atomicExch(info, 1);
+    }
+    __syncthreads();
+    const int p = p_sh;
+    if (p != k)
+      for (int col = threadIdx.x; col < n; col += blockDim.x) {
+        float* ac = A + (long long)col * n;
+        const float t = ac[k];
+        ac[k] = ac[p];
+        ac[p] = t;
+      }
+    __syncthreads();
+    const float inv = 1.0f / A[(long long)k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(long long)k * n + i] *= inv;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (long long t = threadIdx.x; t < (long long)m * m; t += blockDim.x) {
+      const int jj = k + 1 + (int)(t / m), ii = k + 1 + (int)(t % m);
+      A[(long long)jj * n + ii] -= A[(long long)k * n + ii] * A[(long long)jj * n + k];
+    }
+    __syncthreads();
+  }
+}
+
+// y = B^{-1} x per element with the LU factors (FP32 arithmetic, FP64 in and out)
+__global__ void k_lu_solve(long long E, int n, const float* __restrict__ blocks, const int* __restrict__ piv,
+                           const double* __restrict__ x, double* __restrict__ y) {
+  extern __shared__ float sx[];
+  const long long e = blockIdx.x;
+  const float* A = blocks + e * (long long)n * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sx[i] = (float)x[e * n + i];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < n; ++k) {
+      const int p = piv[e * n + k];
+      if (p != k) {
+        const float t = sx[k];
+        sx[k] = sx[p];
+        sx[p] = t;
+      }
+    }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const float xk = sx[k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) sx[i] -= A[(long long)k * n + i] * xk;
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    if (threadIdx.x == 0) sx[k] /= A[(long long)k * n + k];
+    __syncthreads();
+    const float xk = sx[k];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sx[i] -= A[(long long)k * n + i] * xk;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[e * n + i] = (double)sx[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// solver storage
+// ------------------------------------------------------------------------------------------
+struct Solver {
+  int restart = 0;
+  long long n = 0;
+  double* V = nullptr;      // [restart + 1][n]
+  double* vec = nullptr;    // named work vectors below, [NV][n]
+  double* partial = nullptr;
+  double* hdev = nullptr;   // [2][MAXK]
+  double* hhost = nullptr;  // pinned [2][MAXK]
+  double* probe = nullptr;  // [n]
+  float* blocks = nullptr;  // [E][5Np][5Np]
+  int* piv = nullptr;
+  int* info = nullptr;
+  bool bj_ready = false;
+  static constexpr int NV = 12;
+  double* v(int i) { return vec + (long long)i * n; }
+};
+
+enum { VU = 0, VKNOWN, VR0, VR1, VR2, VG, VRES, VZ, VW, VDU, VTMP, VUN };
+
+static void solver_free(Solver* S) {
+  if (!S) return;
+  void* ptrs[] = {S->V, S->vec, S->partial, S->hdev, S->probe, S->blocks, S->piv, S->info};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (S->hhost) cudaFreeHost(S->hhost);
+  delete S;
+}
+
+}  // namespace dg
+
+void dg_solver_release(dg_mesh* m) {
+  dg::solver_free(m->solver);
+  m->solver = nullptr;
+}
+
+namespace dg {
+
+static int solver_get(dg_mesh* m, int restart, Solver** out) {
+  if (restart < 1 || restart >= MAXK) return fail(DG_EINVAL, "gmres restart must be in 1..63");
+  Solver* S = m->solver;
+  if (S && S->restart >= restart) {
+    *out = S;
+    return DG_OK;
+  }
+  dg_solver_release(m);
+  S = new Solver();
+  S->restart = restart;
+  S->n = m->ndof;
+  cudaError_t err = cudaMalloc(&S->V, sizeof(double) * (size_t)(restart + 1) * S->n);
+  if (err == cudaSuccess) err = cudaMalloc(&S->vec, sizeof(double) * (size_t)Solver::NV * S->n);
+  if (err == cudaSuccess) err = cudaMalloc(&S->partial, sizeof(double) * RED_BLOCKS * MAXK);
+  if (err == cudaSuccess) err = cudaMalloc(&S->hdev, sizeof(double) * 2 * MAXK);
+  if (err == cudaSuccess) err = cudaMallocHost(&S->hhost, sizeof(double) * 2 * MAXK);
+  if (err != cudaSuccess) {
+    solver_free(S);
+    return fail(DG_ENOMEM, std::string("solver storage: ") + cudaGetErrorString(err));
+  }
+  m->solver = S;
+  *out = S;
+  return DG_OK;
+}
+
+static int ensure_blocks(dg_mesh* m, Solver* S) {
+  if (S->blocks) return DG_OK;
+  const long long nb = 5LL * m->np;
+  cudaError_t err = cudaMalloc(&S->blocks, sizeof(float) * (size_t)m->E * nb * nb);
+  if (err == cudaSuccess) err = cudaMalloc(&S->piv, sizeof(int) * (size_t)m->E * nb);
+  if (err == cudaSuccess) err = cudaMalloc(&S->info, sizeof(int));
+  if (err == cudaSuccess) err = cudaMalloc(&S->probe, sizeof(double) * (size_t)m->ndof);
+  if (err == cudaSuccess && !m->ws.qx) err = cudaMalloc(&m->ws.qx, sizeof(double) * (size_t)m->E * 90 * m->nf);
+  if (err != cudaSuccess) return fail(DG_ENOMEM, std::string("block-Jacobi storage: ") + cudaGetErrorString(err));
+  return DG_OK;
+}
+
+#define DG_DISPATCH_S(m, call)                                 \
+  switch ((m)->n) {                                            \
+    case 2: rc = Driver<2>::call; break;                       \
+    case 3: rc = Driver<3>::call; break;                       \
+    case 4: rc = Driver<4>::call; break;                       \
+    case 5: rc = Driver<5>::call; break;                       \
+    default: rc = fail(DG_EINVAL, "unsupported degree");       \
+  }
+
+static unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+}
+
+// J_G v = M v - c J_r(U) v
+static int stage_matvec(dg_mesh* m, Solver* S, const double* U, double t, double c, int jv_mode,
+                        const double* v, double* out, cudaStream_t s) {
+  double* mv = S->v(VTMP);
+  int rc = dg_mass_apply(m, v, mv, s);
+  if (rc) return rc;
+  rc = dg_jvp(m, U, v, t, jv_mode, 0.0, out, nullptr, s);
+  if (rc) return rc;
+  prof_begin(m, s, KK_BLAS);
+  k_lincomb<<<grid_for(S->n), 256, 0, s>>>(S->n, 1.0, mv, -c, out, 0.0, nullptr, out);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_lincomb");
+  return DG_OK;
+}
+
+// squared 2-norm on the device, read back (synchronises the stream)
+static int norm2(dg_mesh* m, Solver* S, const double* x, double* out, cudaStream_t s) {
+  prof_begin(m, s, KK_BLAS);
+  k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(S->n, 0, S->V, S->n, x, S->partial);
+  k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev, 0);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_mdot");
+  DG_CUDA_TRY(cudaMemcpyAsync(S->hhost, S->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = std::sqrt(S->hhost[0]);
+  return DG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// preconditioner
+// ------------------------------------------------------------------------------------------
+// exact diagonal blocks of J_G = M - c J_r(U), column j of every element per sweep, into dest
+static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double c, float* dest, cudaStream_t s) {
+  int rc = ensure_blocks(m, S);
+  if (rc) return rc;
+  const int nb = 5 * m->np;
+  double* jv = S->v(VW);
+  double* mv = S->v(VTMP);
+  for (int j = 0; j < nb; ++j) {
+    prof_begin(m, s, KK_BLAS);
+    k_probe<<<grid_for(S->n), 256, 0, s>>>(m->E, nb, j, S->probe);
+    prof_end(m, s);
+    DG_DISPATCH_S(m, jv_blockdiag(m, U, S->probe, t, jv, s));
+    if (rc) return rc;
+    rc = dg_mass_apply(m, S->probe, mv, s);
+    if (rc) return rc;
+    prof_begin(m, s, KK_BLAS);
+    k_scatter_col<<<grid_for(S->n), 256, 0, s>>>(m->E, nb, j, c, mv, jv, dest);
+    prof_end(m, s);
+    DG_LAUNCH_CHECK("k_scatter_col");
+  }
+  return DG_OK;
+}
+
+static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, cudaStream_t s) {
+  int rc = ensure_blocks(m, S);
+  if (rc) return rc;
+  const int nb = 5 * m->np;
+  DG_CUDA_TRY(cudaMemsetAsync(S->info, 0, sizeof(int), s));
+  rc = bj_assemble(m, S, U, t, c, S->blocks, s);
+  if (rc) return rc;
+  prof_begin(m, s, KK_LU);
+  k_lu<<<(unsigned)m->E, 256, 0, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_lu");
+  int info = 0;
+  DG_CUDA_TRY(cudaMemcpyAsync(&info, S->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DG_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) return fail(DG_ENAN, "block-Jacobi: a zero pivot in a diagonal block");
+  S->bj_ready = true;
+  return DG_OK;
+}
+
+static int precond_apply(dg_mesh* m, Solver* S, int kind, const double* x, double* y, cudaStream_t s) {
+  if (kind == DG_PC_NONE) {
+    if (x != y) DG_CUDA_TRY(cudaMemcpyAsync(y, x, sizeof(double) * S->n, cudaMemcpyDeviceToDevice, s));
+    return DG_OK;
+  }
+  if (kind == DG_PC_BJ) {
+    if (!S->bj_ready) return fail(DG_EINVAL, "block-Jacobi preconditioner used before dg_precond_setup");
+    const int nb = 5 * m->np;
+    prof_begin(m, s, KK_PRECOND);
+    k_lu_solve<<<(unsigned)m->E, 128, sizeof(float) * nb, s>>>(m->E, nb, S->blocks, S->piv, x, y);
+    prof_end(m, s);
+    DG_LAUNCH_CHECK("k_lu_solve");
+    return DG_OK;
+  }
+  return fail(DG_EINVAL, "unknown preconditioner kind");
+}
+
+// ------------------------------------------------------------------------------------------
+// GMRES(restart), right preconditioned: solves J_G x = b to ||b - J_G x|| <= tol ||b||
+// ------------------------------------------------------------------------------------------
+static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U, double t, double c,
+                 const double* b, double* x, int* iters, cudaStream_t s) {
+  const long long n = S->n;
+  const int R = o.gmres_restart;
+  double* V = S->V;
+  double* w = S->v(VW);
+  double* z = S->v(VZ);
+  double* r = S->v(VRES);
+  double bnorm = 0.0;
+  int rc = norm2(m, S, b, &bnorm, s);
+  if (rc) return rc;
+  if (!std::isfinite(bnorm)) return fail(DG_ENAN, "GMRES: non-finite right-hand side");
+  DG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  if (bnorm == 0.0) return DG_OK;
+  std::vector<double> H((size_t)(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
+  for (int cycle = 0; cycle < o.max_restarts; ++cycle) {
+    // r = b - A x
+    if (cycle == 0) {
+      DG_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      rc = stage_matvec(m, S, U, t, c, o.jv_mode, x, w, s);
+      if (rc) return rc;
+      k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, b, -1.0, w, 0.0, nullptr, r);
+      DG_LAUNCH_CHECK("k_lincomb");
+    }
+    double beta = 0.0;
+    rc = norm2(m, S, r, &beta, s);
+    if (rc) return rc;
+    if (!std::isfinite(beta)) return fail(DG_ENAN, "GMRES: non-finite residual");
+    if (beta <= o.gmres_rtol * bnorm) return DG_OK;
+    k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0 / beta, r, 0.0, nullptr, 0.0, nullptr, V);
+    DG_LAUNCH_CHECK("k_lincomb");
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kdone = 0;
+    bool converged = false;
+    for (int k = 0; k < R; ++k) {
+      rc = precond_apply(m, S, o.precond, V + (long long)k * n, z, s);
+      if (rc) return rc;
+      rc = stage_matvec(m, S, U, t, c, o.jv_mode, z, w, s);
+      if (rc) return rc;
+      // classical Gram-Schmidt twice; h and the norm stay on the device until one read-back
+      prof_begin(m, s, KK_BLAS);
+      k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k + 1, V, n, w, S->partial);
+      k_mdot_finish<<<1, MAXK, 0, s>>>(k + 1, S->partial, S->hdev, 0);
+      k_maxpy<<<grid_for(n), 256, 0, s>>>(n, k + 1, V, n, S->hdev, w);
+      k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k + 1, V, n, w, S->partial);
+      k_mdot_finish<<<1, MAXK, 0, s>>>(k + 1, S->partial, S->hdev + MAXK, 0);
+      k_maxpy<<<grid_for(n), 256, 0, s>>>(n, k + 1, V, n, S->hdev + MAXK, w);
+      k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, 0, V, n, w, S->partial);
+      k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev + MAXK + k + 1, 0);
+      k_scale_dev<<<grid_for(n), 256, 0, s>>>(n, w, S->hdev + MAXK + k + 1, V + (long long)(k + 1) * n);
+      prof_end(m, s);
+      DG_LAUNCH_CHECK("arnoldi");
+      DG_CUDA_TRY(cudaMemcpyAsync(S->hhost, S->hdev, sizeof(double) * 2 * MAXK, cudaMemcpyDeviceToHost, s));
+      DG_CUDA_TRY(cudaStreamSynchronize(s));
+      double* Hk = &H[(size_t)k * (R + 1)];   // column k, rows 0..k+1
+      for (int j = 0; j <= k; ++j) Hk[j] = S->hhost[j] + S->hhost[MAXK + j];
+      Hk[k + 1] = std::sqrt(S->hhost[MAXK + k + 1]);
+      for (int j = 0; j < k; ++j) {
+        const double t1 = cs[j] * Hk[j] + sn[j] * Hk[j + 1];
+        Hk[j + 1] = -sn[j] * Hk[j] + cs[j] * Hk[j + 1];
+        Hk[j] = t1;
+      }
+      const double den = std::hypot(Hk[k], Hk[k + 1]);
+      if (!std::isfinite(den)) return fail(DG_ENAN, "GMRES: non-finite Arnoldi coefficient");
+      cs[k] = den > 0 ? Hk[k] / den : 1.0;
+      sn[k] = den > 0 ? Hk[k + 1] / den : 0.0;
+      Hk[k] = den;
+      Hk[k + 1] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      ++*iters;
+      kdone = k + 1;
+      if (std::fabs(g[k + 1]) <= o.gmres_rtol * bnorm) {
+        converged = true;
+        break;
+      }
+    }
+    for (int i = kdone - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int j = i + 1; j < kdone; ++j) sum -= H[(size_t)j * (R + 1) + i] * y[j];
+      y[i] = sum / H[(size_t)i * (R + 1) + i];
+    }
+    std::memcpy(S->hhost, y.data(), sizeof(double) * kdone);
+    DG_CUDA_TRY(cudaMemcpyAsync(S->hdev, S->hhost, sizeof(double) * kdone, cudaMemcpyHostToDevice, s));
+    k_combine<<<grid_for(n), 256, 0, s>>>(n, kdone, V, n, S->hdev, r);
+    DG_LAUNCH_CHECK("k_combine");
+    rc = precond_apply(m, S, o.precond, r, z, s);
+    if (rc) return rc;
+    k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, x, 1.0, z, 0.0, nullptr, x);
+    DG_LAUNCH_CHECK("k_lincomb");
+    if (converged) return DG_OK;
+  }
+  return fail(DG_ENOTCONV, "GMRES did not reach its tolerance within max_restarts cycles");
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" void dg_solver_opts_default(dg_solver_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->stages = 3;
+  o->gmres_restart = 30;
+  o->max_restarts = 10;
+  o->max_newton = 20;
+  o->precond = DG_PC_NONE;
+  o->precond_refresh = DG_REFRESH_STEP;
+  o->jv_mode = DG_JV_EXACT;
+  o->newton_rtol = 1e-8;
+  o->gmres_rtol = 1e-3;
+  o->abs_floor = 1e-14;
+}
+
+extern "C" int dg_precond_setup(dg_mesh* mesh, int32_t kind, const double* u, double t, double dt_aii,
+                                void* stream) {
+  if (!mesh || !u) return fail(DG_EINVAL, "dg_precond_setup: null argument");
+  Solver* S = nullptr;
+  int rc = solver_get(mesh, mesh->solver ? mesh->solver->restart : 30, &S);
+  if (rc) return rc;
+  if (kind == DG_PC_NONE) return DG_OK;
+  if (kind == DG_PC_BJ) return bj_setup(mesh, S, u, t, dt_aii, (cudaStream_t)stream);
+  return fail(DG_EINVAL, "dg_precond_setup: unknown kind");
+}
+
+extern "C" int dg_precond_apply(dg_mesh* mesh, int32_t kind, const double* x, double* y, void* stream) {
+  if (!mesh || !x || !y) return fail(DG_EINVAL, "dg_precond_apply: null argument");
+  if (!mesh->solver) return fail(DG_EINVAL, "dg_precond_apply: no preconditioner was set up");
+  return precond_apply(mesh, mesh->solver, kind, x, y, (cudaStream_t)stream);
+}
+
+extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, const dg_solver_opts* opts,
+                                dg_step_stats* stats, void* stream) {
+  if (!mesh || !u || !opts) return fail(DG_EINVAL, "dg_implicit_step: null argument");
+  const dg_solver_opts o = *opts;
+  cudaStream_t s = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  double A[3][3], c[3];
+  int rc = dirk_tableau(o.stages, A, c);
+  if (rc) return rc;
+  if (o.max_newton < 1 || o.max_restarts < 1) return fail(DG_EINVAL, "dg_implicit_step: bad limits");
+  Solver* S = nullptr;
+  rc = solver_get(mesh, o.gmres_restart, &S);
+  if (rc) return rc;
+  dg_step_stats st;
+  std::memset(&st, 0, sizeof(st));
+  const long long n = S->n;
+  double* U = S->v(VU);
+  double* known = S->v(VKNOWN);
+  double* G = S->v(VG);
+  double* res = S->v(VRES);
+  double* dU = S->v(VDU);
+  double* un = S->v(VUN);
+  double* R[3] = {S->v(VR0), S->v(VR1), S->v(VR2)};
+  DG_CUDA_TRY(cudaMemcpyAsync(un, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  DG_CUDA_TRY(cudaMemcpyAsync(U, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  double* Mun = S->v(VTMP);
+  auto finish = [&](int code) {
+    st.status = code;
+    st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = st;
+    return code;
+  };
+  if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_STEP) {
+    const auto p0 = std::chrono::steady_clock::now();
+    rc = bj_setup(mesh, S, un, t + c[0] * dt, dt * A[0][0], s);
+    st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
+    if (rc) return finish(rc);
+  }
+  for (int i = 0; i < o.stages; ++i) {
+    const double ti = t + c[i] * dt, ci = dt * A[i][i];
+    // known = M u_n + dt sum_{j<i} a_ij R_j
+    rc = dg_mass_apply(mesh, un, Mun, s);
+    if (rc) return finish(rc);
+    k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, Mun, i > 0 ? dt * A[i][0] : 0.0, i > 0 ? R[0] : nullptr,
+                                          i > 1 ? dt * A[i][1] : 0.0, i > 1 ? R[1] : nullptr, known);
+    DG_LAUNCH_CHECK("k_lincomb");
+    if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_STAGE) {
+      const auto p0 = std::chrono::steady_clock::now();
+      rc = bj_setup(mesh, S, U, ti, ci, s);
+      st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
+      if (rc) return finish(rc);
+    }
+    double g0 = -1.0;
+    bool done = false;
+    for (int it = 0; it <= o.max_newton; ++it) {
+      rc = dg_residual(mesh, U, nullptr, ti, res, s);
+      if (rc) return finish(rc);
+      rc = dg_mass_apply(mesh, U, G, s);
+      if (rc) return finish(rc);
+      double mun = 0.0;
+      rc = norm2(mesh, S, G, &mun, s);
+      if (rc) return finish(rc);
+      k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, G, -1.0, known, -ci, res, G);
+      DG_LAUNCH_CHECK("k_lincomb");
+      double gn = 0.0;
+      rc = norm2(mesh, S, G, &gn, s);
+      if (rc) return finish(rc);
+      if (!std::isfinite(gn)) return finish(fail(DG_ENAN, "Newton: non-finite stage residual"));
+      if (st.n_hist < DG_STATS_HIST) st.res_hist[st.n_hist++] = gn;
+      if (g0 < 0) g0 = gn;
+      if (gn <= o.newton_rtol * g0 || gn <= o.abs_floor * mun) {
+        st.newton_iters[i] = it;
+        done = true;
+        break;
+      }
+      if (it == o.max_newton) break;
+      if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_NEWTON) {
+        const auto p0 = std::chrono::steady_clock::now();
+        rc = bj_setup(mesh, S, U, ti, ci, s);
+        st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
+        if (rc) return finish(rc);
+      }
+      // dU = -J_G^{-1} G
+      k_lincomb<<<grid_for(n), 256, 0, s>>>(n, -1.0, G, 0.0, nullptr, 0.0, nullptr, G);
+      DG_LAUNCH_CHECK("k_lincomb");
+      int gits = 0;
+      rc = gmres(mesh, S, o, U, ti, ci, G, dU, &gits, s);
+      st.gmres_iters[i] += gits;
+      if (rc) return finish(rc);
+      k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, U, 1.0, dU, 0.0, nullptr, U);
+      DG_LAUNCH_CHECK("k_lincomb");
+    }
+    if (!done) return finish(fail(DG_ENOTCONV, "Newton did not reach its tolerance"));
+    if (i + 1 < o.stages) {
+      rc = dg_residual(mesh, U, nullptr, ti, R[i], s);
+      if (rc) return finish(rc);
+    }
+  }
+  DG_CUDA_TRY(cudaMemcpyAsync(u, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  DG_CUDA_TRY(cudaStreamSynchronize(s));
+  return finish(DG_OK);
+}
+
+extern "C" int dg_dirk_tableau(int32_t stages, double* a, double* c) {
+  if (!a || !c) return fail(DG_EINVAL, "dg_dirk_tableau: null argument");
+  double A[3][3], cc[3];
+  int rc = dirk_tableau(stages, A, cc);
+  if (rc) return rc;
+  for (int i = 0; i < stages; ++i) {
+    c[i] = cc[i];
+    for (int j = 0; j < stages; ++j) a[i * stages + j] = A[i][j];
+  }
+  return DG_OK;
+}
+
+extern "C" int dg_block_assemble(dg_mesh* mesh, const double* u, double t, double dt_aii, float* out,
+                                 void* stream) {
+  if (!mesh || !u || !out) return fail(DG_EINVAL, "dg_block_assemble: null argument");
+  Solver* S = nullptr;
+  int rc = solver_get(mesh, mesh->solver ? mesh->solver->restart : 30, &S);
+  if (rc) return rc;
+  return bj_assemble(mesh, S, u, t, dt_aii, out, (cudaStream_t)stream);
+}

@@ -35,6 +35,26 @@ class DgMeshDesc(ctypes.Structure):
     ]
 
 
+class DgSolverOpts(ctypes.Structure):
+    _fields_ = [
+        ("stages", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
+        ("max_newton", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_refresh", ctypes.c_int32),
+        ("jv_mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("newton_rtol", ctypes.c_double),
+        ("gmres_rtol", ctypes.c_double), ("abs_floor", ctypes.c_double),
+    ]
+
+
+class DgStepStats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32 * 3), ("gmres_iters", ctypes.c_int32 * 3),
+        ("n_hist", ctypes.c_int32), ("res_hist", ctypes.c_double * 64), ("wall_ms", ctypes.c_double),
+        ("precond_ms", ctypes.c_double),
+    ]
+
+
+PC = {"none": 0, "bj": 1, "mlp": 2}
+REFRESH = {"step": 0, "stage": 1, "newton": 2}
+
 _lib = None
 
 
@@ -70,6 +90,13 @@ def lib():
     L.dg_kernel_name.argtypes = [i32]
     L.dg_kernel_name.restype = ctypes.c_char_p
     L.dg_probe_fp64.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    L.dg_solver_opts_default.argtypes = [ctypes.POINTER(DgSolverOpts)]
+    L.dg_solver_opts_default.restype = None
+    L.dg_dirk_tableau.argtypes = [i32, dp, dp]
+    L.dg_implicit_step.argtypes = [vp, dp, d, d, ctypes.POINTER(DgSolverOpts), ctypes.POINTER(DgStepStats), vp]
+    L.dg_precond_setup.argtypes = [vp, i32, dp, d, d, vp]
+    L.dg_precond_apply.argtypes = [vp, i32, dp, dp, vp]
+    L.dg_block_assemble.argtypes = [vp, dp, d, d, dp, vp]
     _lib = L
     return L
 
@@ -202,3 +229,73 @@ def probe_fp64():
     t = ctypes.c_double()
     _check(lib().dg_probe_fp64(ctypes.byref(t)))
     return t.value
+
+
+def solver_opts(**kw):
+    """dg_solver_opts with the library defaults, overridden by keyword (precond and
+    precond_refresh accept the names of PC / REFRESH)."""
+    o = DgSolverOpts()
+    lib().dg_solver_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precond" and isinstance(v, str):
+            v = PC[v]
+        if k == "precond_refresh" and isinstance(v, str):
+            v = REFRESH[v]
+        if k == "jv_mode" and isinstance(v, str):
+            v = DG_JV_EXACT if v == "exact" else DG_JV_FD
+        setattr(o, k, v)
+    return o
+
+
+def dirk_tableau(stages):
+    import numpy as np
+    a = np.zeros(stages * stages)
+    c = np.zeros(stages)
+    _check(lib().dg_dirk_tableau(stages, a.ctypes.data_as(ctypes.c_void_p), c.ctypes.data_as(ctypes.c_void_p)))
+    return a.reshape(stages, stages), c
+
+
+def _stats_dict(st):
+    return {"status": st.status, "newton": list(st.newton_iters), "gmres": list(st.gmres_iters),
+            "res_hist": list(st.res_hist[: st.n_hist]), "wall_ms": st.wall_ms, "precond_ms": st.precond_ms}
+
+
+def _mesh_implicit_step(self, u, t, dt, opts=None, check=True, **kw):
+    """One DIRK step in place on u; returns the statistics (raises on failure when check)."""
+    o = opts if opts is not None else solver_opts(**kw)
+    st = DgStepStats()
+    rc = lib().dg_implicit_step(self._h, _ptr(u, self.u_shape, "u"), float(t), float(dt), ctypes.byref(o),
+                                ctypes.byref(st), _stream())
+    if check:
+        _check(rc)
+    out = _stats_dict(st)
+    out["rc"] = rc
+    return out
+
+
+def _mesh_precond_setup(self, kind, u, t, dt_aii):
+    _check(lib().dg_precond_setup(self._h, PC[kind] if isinstance(kind, str) else kind,
+                                  _ptr(u, self.u_shape, "u"), float(t), float(dt_aii), _stream()))
+
+
+def _mesh_precond_apply(self, kind, x, out=None):
+    y = out if out is not None else self.empty()
+    _check(lib().dg_precond_apply(self._h, PC[kind] if isinstance(kind, str) else kind,
+                                  _ptr(x, self.u_shape, "x"), _ptr(y, self.u_shape, "y"), _stream()))
+    return y
+
+
+def _mesh_block_assemble(self, u, t, dt_aii):
+    """Exact diagonal blocks of J_G as a row-major FP32 tensor [n_elem][5 n_p][5 n_p]."""
+    import torch
+    nb = 5 * self.n_p
+    out = torch.empty((self.n_elem, nb, nb), dtype=torch.float32, device="cuda")
+    _check(lib().dg_block_assemble(self._h, _ptr(u, self.u_shape, "u"), float(t), float(dt_aii),
+                                   ctypes.c_void_p(out.data_ptr()), _stream()))
+    return out.transpose(1, 2)
+
+
+Mesh.implicit_step = _mesh_implicit_step
+Mesh.precond_setup = _mesh_precond_setup
+Mesh.precond_apply = _mesh_precond_apply
+Mesh.block_assemble = _mesh_block_assemble

@@ -23,21 +23,23 @@ def test_exports_every_declared_symbol(libpath):
     assert not missing, missing
 
 
-def test_descriptor_layout_matches_header(tmp_path):
-    """ctypes mirror of dg_mesh_desc has the C layout (size and every field offset)."""
-    fields = [f for f, _ in DG.DgMeshDesc._fields_]
+@pytest.mark.parametrize("cname,pytype", [("dg_mesh_desc", DG.DgMeshDesc), ("dg_solver_opts", DG.DgSolverOpts),
+                                          ("dg_step_stats", DG.DgStepStats)])
+def test_struct_layouts_match_header(tmp_path, cname, pytype):
+    """ctypes mirrors of the ABI structs have the C layout (size and every field offset)."""
+    fields = [f for f, _ in pytype._fields_]
     src = tmp_path / "layout.c"
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.abspath(DG.HEADER)}"',
-             "int main(void) {", 'printf("%zu\\n", sizeof(dg_mesh_desc));']
-    lines += [f'printf("%zu\\n", offsetof(dg_mesh_desc, {f}));' for f in fields]
+             "int main(void) {", f'printf("%zu\\n", sizeof({cname}));']
+    lines += [f'printf("%zu\\n", offsetof({cname}, {f}));' for f in fields]
     lines += ["return 0; }"]
     src.write_text("\n".join(lines))
     exe = tmp_path / "layout"
     subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
     out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    assert out[0] == ctypes.sizeof(DG.DgMeshDesc)
+    assert out[0] == ctypes.sizeof(pytype)
     for f, off in zip(fields, out[1:]):
-        assert getattr(DG.DgMeshDesc, f).offset == off, f
+        assert getattr(pytype, f).offset == off, f
 
 
 def test_descriptor_roundtrip():
