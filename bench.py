@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--implicit", action="store_true",
+                    help="time the implicit DIRK step variants instead (configs shell32x16_p2_euv, shell48x16_p3_euv)")
+    ap.add_argument("--variants", default="plain_bj,mixed_bj,plain_none",
+                    help="comma list for --implicit: plain_bj, mixed_bj, plain_none, mixed_mlp")
     return ap.parse_args()
 
 
@@ -317,8 +321,76 @@ def main_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def main_implicit(args):
+    """Wall time per implicit DIRK(3,3) step of 60 s for the solver variants (1 GPU).
+
+    plain_bj:   FP64 residual and exact FP64 Jv, block-Jacobi on exact blocks (FP32 LU)
+    mixed_bj:   FP64 residual, FP32 inner Jv and FP32-assembled blocks (FP32 LU)
+    plain_none: FP64 unpreconditioned GMRES(30)
+    Every variant starts from the same state; the final states are compared with plain_bj.
+    """
+    import numpy as np
+    import torch
+    from paper_2306_01085_gb300 import build as B
+    from paper_2306_01085_gb300 import dg as DG
+    from paper_2306_01085_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    config = args.config if args.config != CONFIG_NAME else "shell32x16_p2_euv"
+    desc = W.CONFIGS[config][0]()
+    mesh = DG.Mesh(desc)
+    u0 = torch.from_numpy(W.state_for(desc, mesh.nodes().cpu().numpy(), 2)).cuda()
+    dt = 60.0 / W.shell_reference().t0
+    variants = {
+        "plain_bj": dict(precond="bj", jv_prec="f64"),
+        "mixed_bj": dict(precond="bj", jv_prec="f32"),
+        "plain_none": dict(precond="none", jv_prec="f64"),
+    }
+    results, finals = {}, {}
+    for name in args.variants.split(","):
+        kw = variants[name]
+        u = u0.clone()
+        steps = []
+        rc = 0
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = mesh.implicit_step(u, k * dt, dt, stages=3, check=False, **kw)
+            torch.cuda.synchronize()
+            st["wall_s"] = time.perf_counter() - t0
+            steps.append(st)
+            rc = st["rc"]
+            if rc != 0:
+                break
+        finals[name] = u.cpu().numpy() if rc == 0 else None
+        newton = [sum(st["newton"]) for st in steps]
+        gmres = [sum(st["gmres"]) for st in steps]
+        results[name] = {"rc": rc, "steps_done": sum(1 for st in steps if st["rc"] == 0),
+                         "wall_s_per_step": [round(st["wall_s"], 4) for st in steps],
+                         "precond_s_per_step": [round(st["precond_ms"] / 1e3, 4) for st in steps],
+                         "newton_per_step": newton, "gmres_per_step": gmres,
+                         "gmres_per_newton": round(sum(gmres) / max(1, sum(newton)), 2)}
+    ref = finals.get("plain_bj")
+    if ref is not None:
+        du = np.abs(ref - u0.cpu().numpy()).max(axis=(0, 2))
+        for name, fin in finals.items():
+            if fin is not None and name != "plain_bj":
+                results[name]["final_diff_rel_to_change"] = (np.abs(fin - ref).max(axis=(0, 2)) / du).tolist()
+    base = results.get("plain_bj", {}).get("wall_s_per_step")
+    out = {"metric": "implicit DIRK(3,3) step wall time at Newton 1e-8", "unit": "s/step", "config": config,
+           "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "dt_s": 60.0, "steps": args.steps, "variants": results}
+    if base and results.get("mixed_bj", {}).get("rc") == 0:
+        out["speedup_mixed_vs_plain"] = round(np.mean(base) / np.mean(results["mixed_bj"]["wall_s_per_step"]), 3)
+    print(json.dumps(out), flush=True)
+    mesh.close()
+
+
 if __name__ == "__main__":
     a = parse()
+    if a.implicit:
+        main_implicit(a)
+        sys.exit(0)
     if a.cpu_worker:
         cpu_worker(a.config, a.steps, a.cpu_worker)
     elif a.impl == "reference":

@@ -132,6 +132,16 @@ int dg_residual(dg_mesh* mesh, const double* u, const double* q, double t, doubl
 int dg_jvp(dg_mesh* mesh, const double* u, const double* v, double t, int32_t mode, double eps,
            double* jv, double* r_out, void* stream);
 
+/*
+ * FP32 variants of dg_residual (q from u) and of the exact dg_jvp: the same discrete operators
+ * with every intermediate (Gauss values, traces, gradient, fluxes, geometry) stored and computed in
+ * FP32, except exp(varrho/2) = sqrt(rho), which is evaluated in FP64 and rounded. Inputs and
+ * outputs are FP64 as above. The first call allocates the FP32 workspace and FP32 copies of the
+ * geometry (synchronises the device once). Used as the inner Jv of the mixed-precision GMRES.
+ */
+int dg_residual_f32(dg_mesh* mesh, const double* u, double t, double* r, void* stream);
+int dg_jvp_f32(dg_mesh* mesh, const double* u, const double* v, double t, double* jv, double* r_out, void* stream);
+
 /* Mass matrix product (M v)_i = sum_j (phi_i, phi_j) v_j per element and variable (Sec. 3.1). */
 int dg_mass_apply(dg_mesh* mesh, const double* v, double* mv, void* stream);
 
@@ -164,6 +174,9 @@ int dg_residual_static(dg_mesh* mesh, const double* u, double t, double* r, void
 #define DG_REFRESH_STAGE  1  /* rebuild at the start of every stage */
 #define DG_REFRESH_NEWTON 2  /* rebuild at every Newton iteration */
 
+#define DG_PREC_F64 0
+#define DG_PREC_F32 1
+
 #define DG_STATS_HIST 64
 
 typedef struct dg_solver_opts {
@@ -174,7 +187,7 @@ typedef struct dg_solver_opts {
     int32_t precond;         /* DG_PC_* */
     int32_t precond_refresh; /* DG_REFRESH_* */
     int32_t jv_mode;         /* DG_JV_EXACT or DG_JV_FD for the GMRES operator */
-    int32_t reserved;
+    int32_t jv_prec;         /* DG_PREC_F64, or DG_PREC_F32: FP32 inner Jv and block assembly (mixed) */
     double newton_rtol;      /* stop when ||G||_2 <= newton_rtol ||G(U^0)||_2 (1e-8) */
     double gmres_rtol;       /* each Newton system to ||b - J x|| <= gmres_rtol ||b|| (1e-3) */
     double abs_floor;        /* or when ||G||_2 <= abs_floor ||M U||_2 (1e-14) */

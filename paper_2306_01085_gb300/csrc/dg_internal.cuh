@@ -77,6 +77,11 @@ enum KernelKind {
   KK_INTERP = 0, KK_GRAD, KK_FACES, KK_VOLUME, KK_TENSOR, KK_BLAS, KK_GEOMETRY, KK_LU, KK_PRECOND, KK_COUNT
 };
 struct Solver;
+template <typename R>
+struct WorkT {
+  R *ug, *uf, *qg, *qf, *fh, *qx;
+  const R *geo, *fgeo, *acc, *xg;
+};
 struct Prof {
   bool on = false;
   int cap = 0, used = 0;
@@ -106,7 +111,13 @@ struct dg_mesh {
   int32_t* face_f = nullptr; // [F] owner local face
   dg::Workspace ws;
   dg::Solver* solver = nullptr;   // implicit-step storage, created on first use
+  dg::WorkT<float> w32 = {};        // FP32 workspace and geometry, created on first FP32 call
+  float* w32_base = nullptr;
 };
+
+namespace dg {
+int ensure_f32(dg_mesh* m);       // allocate and fill the FP32 workspace and geometry
+}
 
 void dg_solver_release(dg_mesh* m);
 
@@ -135,14 +146,20 @@ inline void prof_end(dg_mesh* m, cudaStream_t s) {
 template <int N>
 struct Driver {
   static int geometry(dg_mesh* m, cudaStream_t s);
-  static int gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s);
+  // f32: FP32 data and arithmetic (exp(log rho) in FP64); inputs and outputs stay FP64
+  static int gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32 = false);
   static int residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
-                      bool tangent, cudaStream_t s);
+                      bool tangent, cudaStream_t s, bool f32 = false);
   static int q_to_nodal(dg_mesh* m, double* q, cudaStream_t s);
   static int q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s);
   static int mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
   // J_r probe restricted to each element's own diagonal block (exact, one column per element)
-  static int jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s);
+  static int jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s,
+                          bool f32 = false);
+  template <typename R> static int gradient_p(dg_mesh* m, const double* u, const double* v, cudaStream_t s);
+  template <typename R> static int residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s);
+  template <typename R>
+  static int jv_blockdiag_p(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s);
 };
 
 // orientation map of face point (is, it) to the neighbour's face point index
@@ -155,38 +172,69 @@ __host__ __device__ inline int orient_map(int o, int is, int it, int n) {
 }
 
 // --------------------------------------------------------------------------------------------
-// forward-mode dual numbers: value and directional derivative
+// forward-mode dual numbers over a real type T: value and directional derivative
 // --------------------------------------------------------------------------------------------
-struct Dual {
-  double v, d;
+template <typename T>
+struct DualT {
+  T v, d;
 };
-__host__ __device__ inline Dual mk(double v, double d) { return Dual{v, d}; }
-__host__ __device__ inline Dual operator+(Dual a, Dual b) { return Dual{a.v + b.v, a.d + b.d}; }
-__host__ __device__ inline Dual operator-(Dual a, Dual b) { return Dual{a.v - b.v, a.d - b.d}; }
-__host__ __device__ inline Dual operator-(Dual a) { return Dual{-a.v, -a.d}; }
-__host__ __device__ inline Dual operator*(Dual a, Dual b) { return Dual{a.v * b.v, a.v * b.d + a.d * b.v}; }
-__host__ __device__ inline Dual operator+(Dual a, double b) { return Dual{a.v + b, a.d}; }
-__host__ __device__ inline Dual operator+(double b, Dual a) { return Dual{a.v + b, a.d}; }
-__host__ __device__ inline Dual operator-(Dual a, double b) { return Dual{a.v - b, a.d}; }
-__host__ __device__ inline Dual operator-(double b, Dual a) { return Dual{b - a.v, -a.d}; }
-__host__ __device__ inline Dual operator*(Dual a, double b) { return Dual{a.v * b, a.d * b}; }
-__host__ __device__ inline Dual operator*(double b, Dual a) { return Dual{a.v * b, a.d * b}; }
+using Dual = DualT<double>;
+template <typename T> __host__ __device__ inline DualT<T> operator+(DualT<T> a, DualT<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <typename T> __host__ __device__ inline DualT<T> operator-(DualT<T> a, DualT<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <typename T> __host__ __device__ inline DualT<T> operator-(DualT<T> a) { return {-a.v, -a.d}; }
+template <typename T> __host__ __device__ inline DualT<T> operator*(DualT<T> a, DualT<T> b) { return {a.v * b.v, a.v * b.d + a.d * b.v}; }
+template <typename T> __host__ __device__ inline DualT<T> operator+(DualT<T> a, T b) { return {a.v + b, a.d}; }
+template <typename T> __host__ __device__ inline DualT<T> operator+(T b, DualT<T> a) { return {a.v + b, a.d}; }
+template <typename T> __host__ __device__ inline DualT<T> operator-(DualT<T> a, T b) { return {a.v - b, a.d}; }
+template <typename T> __host__ __device__ inline DualT<T> operator-(T b, DualT<T> a) { return {b - a.v, -a.d}; }
+template <typename T> __host__ __device__ inline DualT<T> operator*(DualT<T> a, T b) { return {a.v * b, a.d * b}; }
+template <typename T> __host__ __device__ inline DualT<T> operator*(T b, DualT<T> a) { return {a.v * b, a.d * b}; }
+
+template <typename S> struct RealOf { using type = S; };
+template <typename T> struct RealOf<DualT<T>> { using type = T; };
 
 __device__ inline double s_exp(double x) { return exp(x); }
-__device__ inline Dual s_exp(Dual x) {
-  double e = exp(x.v);
-  return Dual{e, e * x.d};
+__device__ inline float s_exp(float x) { return expf(x); }
+template <typename T> __device__ inline DualT<T> s_exp(DualT<T> x) {
+  const T e = s_exp(x.v);
+  return {e, e * x.d};
 }
 __device__ inline double s_log(double x) { return log(x); }
-__device__ inline Dual s_log(Dual x) { return Dual{log(x.v), x.d / x.v}; }
-__device__ inline double s_val(double x) { return x; }
-__device__ inline double s_val(Dual x) { return x.v; }
-template <typename S> __device__ inline S s_zero();
-template <> __device__ inline double s_zero<double>() { return 0.0; }
-template <> __device__ inline Dual s_zero<Dual>() { return Dual{0.0, 0.0}; }
-template <typename S> __device__ inline S s_const(double c);
+__device__ inline float s_log(float x) { return logf(x); }
+template <typename T> __device__ inline DualT<T> s_log(DualT<T> x) { return {s_log(x.v), x.d / x.v}; }
+// exponential evaluated in FP64 whatever the working precision (exp(log rho) stays FP64)
+__device__ inline double s_exp64(double x) { return exp(x); }
+__device__ inline float s_exp64(float x) { return (float)exp((double)x); }
+template <typename T> __device__ inline DualT<T> s_exp64(DualT<T> x) {
+  const T e = s_exp64(x.v);
+  return {e, e * x.d};
+}
+template <typename S> __device__ inline S s_zero() { return S{}; }
+template <typename S> __device__ inline S s_const(typename RealOf<S>::type c);
 template <> __device__ inline double s_const<double>(double c) { return c; }
-template <> __device__ inline Dual s_const<Dual>(double c) { return Dual{c, 0.0}; }
+template <> __device__ inline float s_const<float>(float c) { return c; }
+template <> __device__ inline Dual s_const<Dual>(double c) { return {c, 0.0}; }
+template <> __device__ inline DualT<float> s_const<DualT<float>>(float c) { return {c, 0.0f}; }
+
+// physics parameters in the working precision
+template <typename R>
+struct PhysT {
+  R gamma, c_mu, c_k, c_d, p_coef, cv, visc_exp, lam, t_wall;
+  R omega[3];
+  R cor;
+  int euv;
+  R euv_amp, euv_inv2s2, euv_r_peak, euv_inv_w, euv_omega_t;
+};
+template <typename R>
+inline PhysT<R> phys_as(const Phys& P) {
+  PhysT<R> q;
+  q.gamma = (R)P.gamma; q.c_mu = (R)P.c_mu; q.c_k = (R)P.c_k; q.c_d = (R)P.c_d; q.p_coef = (R)P.p_coef;
+  q.cv = (R)P.cv; q.visc_exp = (R)P.visc_exp; q.lam = (R)P.lam; q.t_wall = (R)P.t_wall;
+  for (int k = 0; k < 3; ++k) q.omega[k] = (R)P.omega[k];
+  q.cor = (R)P.cor; q.euv = P.euv; q.euv_amp = (R)P.euv_amp; q.euv_inv2s2 = (R)P.euv_inv2s2;
+  q.euv_r_peak = (R)P.euv_r_peak; q.euv_inv_w = (R)P.euv_inv_w; q.euv_omega_t = (R)P.euv_omega_t;
+  return q;
+}
 
 // --------------------------------------------------------------------------------------------
 // pointwise physics (Eq. fluxSWNondimensional): flux F[c][d], source s[c]
@@ -197,26 +245,26 @@ struct Prim {
   S isr, v[3], T, gv[3][3], gT[3], div, eps[3][3], mu;
 };
 
-template <typename S>
-__device__ inline void primitives(const Phys& P, const S u[5], const S q[3][5], Prim<S>& w) {
-  w.isr = s_exp(-0.5 * u[0]);
+template <typename S, typename R = typename RealOf<S>::type>
+__device__ inline void primitives(const PhysT<R>& P, const S u[5], const S q[3][5], Prim<S>& w) {
+  w.isr = s_exp64(R(-0.5) * u[0]);
   for (int m = 0; m < 3; ++m) w.v[m] = u[1 + m] * w.isr;
   w.T = u[4] * w.isr;
   for (int m = 0; m < 3; ++m)
-    for (int d = 0; d < 3; ++d) w.gv[m][d] = w.isr * (q[d][1 + m] - 0.5 * (u[1 + m] * q[d][0]));
-  for (int d = 0; d < 3; ++d) w.gT[d] = w.isr * (q[d][4] - 0.5 * (u[4] * q[d][0]));
+    for (int d = 0; d < 3; ++d) w.gv[m][d] = w.isr * (q[d][1 + m] - R(0.5) * (u[1 + m] * q[d][0]));
+  for (int d = 0; d < 3; ++d) w.gT[d] = w.isr * (q[d][4] - R(0.5) * (u[4] * q[d][0]));
   w.div = w.gv[0][0] + w.gv[1][1] + w.gv[2][2];
   for (int m = 0; m < 3; ++m)
     for (int d = 0; d < 3; ++d) w.eps[m][d] = w.gv[m][d] + w.gv[d][m];
-  for (int m = 0; m < 3; ++m) w.eps[m][m] = w.eps[m][m] - (2.0 / 3.0) * w.div;
-  w.mu = (P.visc_exp != 0.0) ? s_exp(P.visc_exp * s_log(w.T)) : s_const<S>(1.0);
+  for (int m = 0; m < 3; ++m) w.eps[m][m] = w.eps[m][m] - R(2.0 / 3.0) * w.div;
+  w.mu = (P.visc_exp != R(0)) ? s_exp(P.visc_exp * s_log(w.T)) : s_const<S>(R(1));
 }
 
-// flux F(u, q) . n  (n: 3 doubles), viscous terms optional
-template <typename S>
-__device__ inline void flux_dot_n(const Phys& P, const S u[5], const S q[3][5], const double n[3],
-                                  bool viscous, S out[5]) {
-  S isr = s_exp(-0.5 * u[0]);
+// flux F(u, q) . n  (n: 3 reals), viscous terms optional
+template <typename S, typename R = typename RealOf<S>::type>
+__device__ inline void flux_dot_n(const PhysT<R>& P, const S u[5], const S q[3][5], const R n[3], bool viscous,
+                                  S out[5]) {
+  S isr = s_exp64(R(-0.5) * u[0]);
   S v[3] = {u[1] * isr, u[2] * isr, u[3] * isr};
   S vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
   out[0] = u[0] * vn;
@@ -234,11 +282,11 @@ __device__ inline void flux_dot_n(const Phys& P, const S u[5], const S q[3][5], 
 }
 
 // stabilisation diagonal sigma(u_hat) = lambda0 + sigma_d (Eq. LDG2)
-template <typename S>
-__device__ inline void sigma_diag(const Phys& P, const S uh[5], S sg[5]) {
-  S isr = s_exp(-0.5 * uh[0]);
+template <typename S, typename R = typename RealOf<S>::type>
+__device__ inline void sigma_diag(const PhysT<R>& P, const S uh[5], S sg[5]) {
+  S isr = s_exp64(R(-0.5) * uh[0]);
   S T = uh[4] * isr;
-  S mu = (P.visc_exp != 0.0) ? s_exp(P.visc_exp * s_log(T)) : s_const<S>(1.0);
+  S mu = (P.visc_exp != R(0)) ? s_exp(P.visc_exp * s_log(T)) : s_const<S>(R(1));
   S sm = P.lam + (P.c_mu * mu) * isr;
   sg[0] = s_const<S>(P.lam);
   sg[1] = sm;
@@ -247,13 +295,13 @@ __device__ inline void sigma_diag(const Phys& P, const S uh[5], S sg[5]) {
   sg[4] = P.lam + ((P.c_k / P.cv) * mu) * isr;
 }
 
-template <typename S>
-__device__ inline void wall_trace(const Phys& P, const S u[5], S ub[5]) {
+template <typename S, typename R = typename RealOf<S>::type>
+__device__ inline void wall_trace(const PhysT<R>& P, const S u[5], S ub[5]) {
   ub[0] = u[0];
   ub[1] = s_zero<S>();
   ub[2] = s_zero<S>();
   ub[3] = s_zero<S>();
-  ub[4] = s_exp(0.5 * u[0]) * P.t_wall;
+  ub[4] = s_exp64(R(0.5) * u[0]) * P.t_wall;
 }
 
 }  // namespace dg

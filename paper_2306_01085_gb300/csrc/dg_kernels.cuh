@@ -51,13 +51,12 @@ __device__ __forceinline__ int pt_stride(int dir) {
 }
 
 // 1D pass along `dir` at point g: sum_k A[i][k] in[.. k ..] (T = false) or A[k][i] (T = true)
-template <int N, bool T>
-__device__ __forceinline__ double line(const double* __restrict__ A, const double* __restrict__ in,
-                                       int g, int dir) {
+template <int N, bool T, typename R>
+__device__ __forceinline__ R line(const R* __restrict__ A, const R* __restrict__ in, int g, int dir) {
   const int st = pt_stride<N>(dir);
   const int i = (g / st) % N;
   const int base = g - i * st;
-  double acc = (T ? A[i] : A[i * N]) * in[base];
+  R acc = (T ? A[i] : A[i * N]) * in[base];
 #pragma unroll
   for (int k = 1; k < N; ++k) acc = fma(T ? A[k * N + i] : A[i * N + k], in[base + k * st], acc);
   return acc;
@@ -89,55 +88,60 @@ __device__ __forceinline__ int axis_index(int g, int axis) {
   return axis == 0 ? g % N : (axis == 1 ? (g / N) % N : g / (N * N));
 }
 
-struct SmemOps {
-  double B[MAXN * MAXN], D[MAXN * MAXN], Binv[MAXN * MAXN], eL[MAXN], eR[MAXN];
+template <typename R>
+struct SmemOpsT {
+  R B[MAXN * MAXN], D[MAXN * MAXN], Binv[MAXN * MAXN], eL[MAXN], eR[MAXN];
 };
+using SmemOps = SmemOpsT<double>;
 
-template <int N>
-__device__ __forceinline__ void load_ops(const Ops* __restrict__ o, SmemOps& s) {
+// the 1D operators (built in FP64 on the host) rounded to the working precision
+template <int N, typename R>
+__device__ __forceinline__ void load_ops(const Ops* __restrict__ o, SmemOpsT<R>& s) {
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    s.B[i] = o->B[i];
-    s.D[i] = o->D[i];
-    s.Binv[i] = o->Binv[i];
+    s.B[i] = (R)o->B[i];
+    s.D[i] = (R)o->D[i];
+    s.Binv[i] = (R)o->Binv[i];
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    s.eL[i] = o->eL[i];
-    s.eR[i] = o->eR[i];
+    s.eL[i] = (R)o->eL[i];
+    s.eR[i] = (R)o->eR[i];
   }
 }
+
 
 // --------------------------------------------------------------------------------------------
 // k_interp: nodal -> Gauss values and face traces. NC = 1 (u) or 2 (u and tangent v).
 // --------------------------------------------------------------------------------------------
-template <int N, int NC>
+template <int N, int NC, typename R>
 __global__ void k_interp(const double* __restrict__ u, const double* __restrict__ v, long long E,
-                         const Ops* __restrict__ ops, double* __restrict__ ug, double* __restrict__ uf) {
+                         const Ops* __restrict__ ops, R* __restrict__ ug, R* __restrict__ uf) {
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
-  __shared__ SmemOps so;
-  extern __shared__ double smem[];
-  double* b0 = smem;                       // [EPB][C][NP]
-  double* b1 = smem + EPB * C * NP;        // [EPB][C][NP]
-  load_ops<N>(ops, so);
+  __shared__ SmemOpsT<R> so;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* smem = reinterpret_cast<R*>(smem_raw);
+  R* b0 = smem;                            // [EPB][C][NP]
+  R* b1 = smem + EPB * C * NP;             // [EPB][C][NP]
+  load_ops<N, R>(ops, so);
   const long long e0 = (long long)blockIdx.x * EPB;
   for (int idx = threadIdx.x; idx < EPB * 5 * NP; idx += blockDim.x) {
     const int el = idx / (5 * NP), rem = idx % (5 * NP);
     const long long e = e0 + el;
     if (e < E) {
-      b0[(el * C) * NP + rem] = u[e * 5 * NP + rem];
-      if (NC == 2) b0[(el * C + 5) * NP + rem] = v[e * 5 * NP + rem];
+      b0[(el * C) * NP + rem] = (R)u[e * 5 * NP + rem];
+      if (NC == 2) b0[(el * C + 5) * NP + rem] = (R)v[e * 5 * NP + rem];
     }
   }
   __syncthreads();
   const int el = threadIdx.x / NP, g = threadIdx.x % NP;
   const bool active = el < EPB;
-  double* in = b0;
-  double* out = b1;
+  R* in = b0;
+  R* out = b1;
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     if (active)
       for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, false>(so.B, in + (el * C + c) * NP, g, dir);
     __syncthreads();
-    double* t = in;
+    R* t = in;
     in = out;
     out = t;
   }
@@ -157,10 +161,10 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
     const int phi = rem / (5 * NF), c = (rem / NF) % 5, f = rem % NF;
     const long long e = e0 + l;
     if (e >= E) continue;
-    const double* ev = (phi & 1) ? so.eR : so.eL;
+    const R* ev = (phi & 1) ? so.eR : so.eL;
     for (int pl = 0; pl < NC; ++pl) {
-      const double* src = in + (l * C + 5 * pl + c) * NP;
-      double acc = 0.0;
+      const R* src = in + (l * C + 5 * pl + c) * NP;
+      R acc = R(0);
 #pragma unroll
       for (int k = 0; k < N; ++k) acc = fma(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
       uf[pl * plane_f + e * 30 * NF + rem] = acc;
@@ -175,21 +179,22 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
 // (u_hat picks up half of the own trace on interior faces) and qx receives, per face, the trace of
 // the gradient tangent this element would get from its neighbour's perturbation across that face:
 // kappa(f) (w n dS)(f) u_dot_nb(f) / 2 with kappa(f) = sum_k e_face[k]^2 / (w |J|)(g(f, k)).
-template <int N, int NC, bool BLK>
-__global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const double* __restrict__ geo,
-                       const double* __restrict__ fgeo, const int* __restrict__ nbr,
-                       const int* __restrict__ nbr_fo, const double* __restrict__ ug,
-                       const double* __restrict__ uf, double* __restrict__ qg, double* __restrict__ qf,
-                       double* __restrict__ qx) {
+template <int N, int NC, bool BLK, typename R>
+__global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, const R* __restrict__ geo,
+                       const R* __restrict__ fgeo, const int* __restrict__ nbr,
+                       const int* __restrict__ nbr_fo, const R* __restrict__ ug,
+                       const R* __restrict__ uf, R* __restrict__ qg, R* __restrict__ qf,
+                       R* __restrict__ qx) {
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
-  __shared__ SmemOps so;
-  extern __shared__ double smem[];
-  double* sU = smem;                        // [EPB][C][NP]
-  double* sUh = sU + EPB * C * NP;          // [EPB][6][C][NF]   U_hat
-  double* sN = sUh + EPB * 6 * C * NF;      // [EPB][6][3][NF]   w n dS
-  double* sY = sN + EPB * 6 * 3 * NF;       // [EPB][9][NP]
-  double* sQ = sY + EPB * 9 * NP;           // [EPB][3][C][NP]
-  load_ops<N>(ops, so);
+  __shared__ SmemOpsT<R> so;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* smem = reinterpret_cast<R*>(smem_raw);
+  R* sU = smem;                             // [EPB][C][NP]
+  R* sUh = sU + EPB * C * NP;               // [EPB][6][C][NF]   U_hat
+  R* sN = sUh + EPB * 6 * C * NF;           // [EPB][6][3][NF]   w n dS
+  R* sY = sN + EPB * 6 * 3 * NF;            // [EPB][9][NP]
+  R* sQ = sY + EPB * 9 * NP;                // [EPB][3][C][NP]
+  load_ops<N, R>(ops, so);
   const long long e0 = (long long)blockIdx.x * EPB;
   const long long plane_g = E * 5 * NP, plane_f = E * 30 * NF;
   for (int idx = threadIdx.x; idx < EPB * 5 * NP; idx += blockDim.x) {
@@ -206,10 +211,10 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const d
     const long long fbase = e * 30 * NF + phi * 5 * NF + f;
     for (int d = 0; d < 3; ++d) sN[((l * 6 + phi) * 3 + d) * NF + f] = fgeo[((e * 6 + phi) * 4 + d) * NF + f];
     const int nb = nbr[e * 6 + phi];
-    double own[10], oth[10];
+    R own[10], oth[10];
     for (int pl = 0; pl < NC; ++pl)
       for (int c = 0; c < 5; ++c) own[5 * pl + c] = uf[pl * plane_f + fbase + c * NF];
-    double* dst = sUh + ((l * 6 + phi) * C) * NF + f;
+    R* dst = sUh + ((l * 6 + phi) * C) * NF + f;
     if (nb >= 0) {
       const int fo = nbr_fo[e * 6 + phi];
       const int f2 = orient_map(fo >> 3, f % N, f / N, N);
@@ -218,42 +223,42 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const d
         for (int c = 0; c < 5; ++c) oth[5 * pl + c] = uf[pl * plane_f + nbase + c * NF];
       if constexpr (BLK) {
         for (int c = 0; c < 5; ++c) {
-          dst[c * NF] = 0.5 * (own[c] + oth[c]);
-          dst[(5 + c) * NF] = 0.5 * own[5 + c];
+          dst[c * NF] = R(0.5) * (own[c] + oth[c]);
+          dst[(5 + c) * NF] = R(0.5) * own[5 + c];
         }
-        const double* ev = (phi & 1) ? so.eR : so.eL;
-        double kappa = 0.0;
+        const R* ev = (phi & 1) ? so.eR : so.eL;
+        R kappa = R(0);
         for (int k = 0; k < N; ++k) kappa += ev[k] * ev[k] / geo[e * 10 * NP + 9 * NP + face_vol_point<N>(phi, f, k)];
-        double* xo = qx + (e * 6 + phi) * 15 * NF + f;
+        R* xo = qx + (e * 6 + phi) * 15 * NF + f;
         for (int d = 0; d < 3; ++d) {
-          const double kn = 0.5 * kappa * fgeo[((e * 6 + phi) * 4 + d) * NF + f];
+          const R kn = R(0.5) * kappa * fgeo[((e * 6 + phi) * 4 + d) * NF + f];
           for (int c = 0; c < 5; ++c) xo[(d * 5 + c) * NF] = kn * oth[5 + c];
         }
       } else {
-        for (int c = 0; c < C; ++c) dst[c * NF] = 0.5 * (own[c] + oth[c]);
+        for (int c = 0; c < C; ++c) dst[c * NF] = R(0.5) * (own[c] + oth[c]);
       }
     } else if (nb == -DG_BC_WALL) {
       if constexpr (BLK) {
-        double* xo = qx + (e * 6 + phi) * 15 * NF + f;
-        for (int k = 0; k < 15; ++k) xo[k * NF] = 0.0;
+        R* xo = qx + (e * 6 + phi) * 15 * NF + f;
+        for (int k = 0; k < 15; ++k) xo[k * NF] = R(0);
       }
-      const double sr = exp(0.5 * own[0]);
+      const R sr = s_exp64(R(0.5) * own[0]);
       dst[0] = own[0];
-      dst[NF] = 0.0;
-      dst[2 * NF] = 0.0;
-      dst[3 * NF] = 0.0;
+      dst[NF] = R(0);
+      dst[2 * NF] = R(0);
+      dst[3 * NF] = R(0);
       dst[4 * NF] = sr * P.t_wall;
       if (NC == 2) {
         dst[5 * NF] = own[5];
-        dst[6 * NF] = 0.0;
-        dst[7 * NF] = 0.0;
-        dst[8 * NF] = 0.0;
-        dst[9 * NF] = 0.5 * sr * P.t_wall * own[5];
+        dst[6 * NF] = R(0);
+        dst[7 * NF] = R(0);
+        dst[8 * NF] = R(0);
+        dst[9 * NF] = R(0.5) * sr * P.t_wall * own[5];
       }
     } else {
       if constexpr (BLK) {
-        double* xo = qx + (e * 6 + phi) * 15 * NF + f;
-        for (int k = 0; k < 15; ++k) xo[k * NF] = 0.0;
+        R* xo = qx + (e * 6 + phi) * 15 * NF + f;
+        for (int k = 0; k < 15; ++k) xo[k * NF] = R(0);
       }
       for (int c = 0; c < C; ++c) dst[c * NF] = own[c];
     }
@@ -261,31 +266,31 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const d
   __syncthreads();
   const int el = threadIdx.x / NP, g = threadIdx.x % NP;
   const bool active = el < EPB && (e0 + el) < E;
-  double G[9], invW = 0.0;
+  R G[9], invW = R(0);
   if (active) {
-    const double* gp = geo + (e0 + el) * 10 * NP + g;
+    const R* gp = geo + (e0 + el) * 10 * NP + g;
     for (int k = 0; k < 9; ++k) G[k] = gp[k * NP];
-    invW = 1.0 / gp[9 * NP];
+    invW = R(1) / gp[9 * NP];
   }
   for (int c = 0; c < C; ++c) {
     if (active) {
-      const double uc = sU[(el * C + c) * NP + g];
+      const R uc = sU[(el * C + c) * NP + g];
       for (int k = 0; k < 9; ++k) sY[(el * 9 + k) * NP + g] = G[k] * uc;
     }
     __syncthreads();
     if (active) {
       // lifting of the traces: sum over the 6 faces of e_face[i_axis] (w n_d dS) u_hat_c
-      double lift[3] = {0.0, 0.0, 0.0};
+      R lift[3] = {R(0), R(0), R(0)};
 #pragma unroll
       for (int phi = 0; phi < 6; ++phi) {
         const int axis = phi >> 1;
-        const double coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
+        const R coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
         const int f = vol_face_point<N>(g, axis);
-        const double uh = sUh[((el * 6 + phi) * C + c) * NF + f];
+        const R uh = sUh[((el * 6 + phi) * C + c) * NF + f];
         for (int d = 0; d < 3; ++d) lift[d] = fma(coef * sN[((el * 6 + phi) * 3 + d) * NF + f], uh, lift[d]);
       }
       for (int d = 0; d < 3; ++d) {
-        double acc = 0.0;
+        R acc = R(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) acc += line<N, true>(so.D, sY + (el * 9 + a * 3 + d) * NP, g, a);
         sQ[((el * 3 + d) * C + c) * NP + g] = (lift[d] - acc) * invW;
@@ -308,10 +313,10 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const d
     const int d = dc / 5, c = dc % 5;
     const long long e = e0 + l;
     if (e >= E) continue;
-    const double* ev = (phi & 1) ? so.eR : so.eL;
+    const R* ev = (phi & 1) ? so.eR : so.eL;
     for (int pl = 0; pl < NC; ++pl) {
-      const double* src = sQ + ((l * 3 + d) * C + 5 * pl + c) * NP;
-      double acc = 0.0;
+      const R* src = sQ + ((l * 3 + d) * C + 5 * pl + c) * NP;
+      R acc = R(0);
 #pragma unroll
       for (int k = 0; k < N; ++k) acc = fma(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
       qf[pl * E * 90 * NF + e * 90 * NF + rem] = acc;
@@ -322,46 +327,44 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, Phys P, const d
 // --------------------------------------------------------------------------------------------
 // k_faces: numerical flux of Eq. LDG2 on every face, written for both element faces
 // --------------------------------------------------------------------------------------------
-template <typename S, int NC>
-__device__ __forceinline__ S ld(const double* p, long long plane) {
+template <typename S, int NC, typename R>
+__device__ __forceinline__ S ld(const R* p, long long plane) {
   if constexpr (NC == 1) return p[0];
-  else return Dual{p[0], p[plane]};
+  else return S{p[0], p[plane]};
 }
-template <typename S>
-__device__ __forceinline__ void st(double* p, long long plane, S v);
-template <>
-__device__ __forceinline__ void st<double>(double* p, long long, double v) { p[0] = v; }
-template <>
-__device__ __forceinline__ void st<Dual>(double* p, long long plane, Dual v) {
+template <typename R>
+__device__ __forceinline__ void st(R* p, long long, R v) { p[0] = v; }
+template <typename R>
+__device__ __forceinline__ void st(R* p, long long plane, DualT<R> v) {
   p[0] = v.v;
   p[plane] = v.d;
 }
 
 // interior numerical flux of Eq. LDG2 with the normal n = w n dS of the first side:
 // F_hat . n = (F(u, q) + F(u2, q2)) . n / 2 + sigma(u_hat) (u - u_hat) |n|, u_hat = (u + u2) / 2
-template <typename S>
-__device__ __forceinline__ void face_flux_interior(const Phys& P, const S u[5], const S q[3][5], const S u2[5],
-                                                   const S q2[3][5], const double n[3], double area, S out[5]) {
+template <typename S, typename R = typename RealOf<S>::type>
+__device__ __forceinline__ void face_flux_interior(const PhysT<R>& P, const S u[5], const S q[3][5], const S u2[5],
+                                                   const S q2[3][5], const R n[3], R area, S out[5]) {
   S f1[5], fn[5], uh[5], sg[5];
   flux_dot_n(P, u, q, n, true, f1);
   flux_dot_n(P, u2, q2, n, true, fn);
 #pragma unroll
-  for (int c = 0; c < 5; ++c) uh[c] = 0.5 * (u[c] + u2[c]);
+  for (int c = 0; c < 5; ++c) uh[c] = R(0.5) * (u[c] + u2[c]);
   sigma_diag(P, uh, sg);
 #pragma unroll
-  for (int c = 0; c < 5; ++c) out[c] = 0.5 * (f1[c] + fn[c]) + sg[c] * ((0.5 * area) * (u[c] - u2[c]));
+  for (int c = 0; c < 5; ++c) out[c] = R(0.5) * (f1[c] + fn[c]) + sg[c] * ((R(0.5) * area) * (u[c] - u2[c]));
 }
 
 // BLK (NC = 2): interior faces evaluate the tangent twice, once for each side's diagonal block:
 // the own side carries its perturbation and the other side only the gradient it receives from it
 // across this face (qx of the other element).
-template <int N, int NC, bool BLK>
-__global__ void k_faces(long long E, long long F, Phys P, const int* __restrict__ face_e,
+template <int N, int NC, bool BLK, typename R>
+__global__ void k_faces(long long E, long long F, PhysT<R> P, const int* __restrict__ face_e,
                         const int* __restrict__ face_f, const int* __restrict__ nbr,
-                        const int* __restrict__ nbr_fo, const double* __restrict__ fgeo,
-                        const double* __restrict__ uf, const double* __restrict__ qf,
-                        const double* __restrict__ qx, double* __restrict__ fh) {
-  using S = typename std::conditional<NC == 2, Dual, double>::type;
+                        const int* __restrict__ nbr_fo, const R* __restrict__ fgeo,
+                        const R* __restrict__ uf, const R* __restrict__ qf,
+                        const R* __restrict__ qx, R* __restrict__ fh) {
+  using S = typename std::conditional<NC == 2, DualT<R>, R>::type;
   constexpr int NF = Shape<N>::NF;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= F * NF) return;
@@ -370,18 +373,18 @@ __global__ void k_faces(long long E, long long F, Phys P, const int* __restrict_
   const long long e = face_e[fi];
   const int phi = face_f[fi];
   const long long plane_u = E * 30 * NF, plane_q = E * 90 * NF;
-  const double* gp = fgeo + ((e * 6 + phi) * 4) * NF + f;
-  const double n[3] = {gp[0], gp[NF], gp[2 * NF]};
-  const double area = gp[3 * NF];
+  const R* gp = fgeo + ((e * 6 + phi) * 4) * NF + f;
+  const R n[3] = {gp[0], gp[NF], gp[2 * NF]};
+  const R area = gp[3 * NF];
   S u[5], q[3][5];
   const long long ub = e * 30 * NF + phi * 5 * NF + f;
   const long long qb = e * 90 * NF + phi * 15 * NF + f;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) u[c] = ld<S, NC>(uf + ub + c * NF, plane_u);
+  for (int c = 0; c < 5; ++c) u[c] = ld<S, NC, R>(uf + ub + c * NF, plane_u);
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
-    for (int c = 0; c < 5; ++c) q[d][c] = ld<S, NC>(qf + qb + (d * 5 + c) * NF, plane_q);
+    for (int c = 0; c < 5; ++c) q[d][c] = ld<S, NC, R>(qf + qb + (d * 5 + c) * NF, plane_q);
   const int nb = nbr[e * 6 + phi];
   S out[5];
   if (nb >= 0) {
@@ -392,37 +395,37 @@ __global__ void k_faces(long long E, long long F, Phys P, const int* __restrict_
     const long long ub2 = (long long)nb * 30 * NF + phi2 * 5 * NF + f2;
     const long long qb2 = (long long)nb * 90 * NF + phi2 * 15 * NF + f2;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) u2[c] = ld<S, NC>(uf + ub2 + c * NF, plane_u);
+    for (int c = 0; c < 5; ++c) u2[c] = ld<S, NC, R>(uf + ub2 + c * NF, plane_u);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int c = 0; c < 5; ++c) q2[d][c] = ld<S, NC>(qf + qb2 + (d * 5 + c) * NF, plane_q);
+      for (int c = 0; c < 5; ++c) q2[d][c] = ld<S, NC, R>(qf + qb2 + (d * 5 + c) * NF, plane_q);
     const long long ob2 = (long long)nb * 30 * NF + phi2 * 5 * NF + f2;
     if constexpr (BLK) {
       // block of the own element: the neighbour side carries only the cross gradient tangent
       S ua[5], qa[3][5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) ua[c] = Dual{u2[c].v, 0.0};
+      for (int c = 0; c < 5; ++c) ua[c] = S{u2[c].v, R(0)};
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int c = 0; c < 5; ++c) qa[d][c] = Dual{q2[d][c].v, qx[((long long)nb * 6 + phi2) * 15 * NF + (d * 5 + c) * NF + f2]};
+        for (int c = 0; c < 5; ++c) qa[d][c] = S{q2[d][c].v, qx[((long long)nb * 6 + phi2) * 15 * NF + (d * 5 + c) * NF + f2]};
       face_flux_interior(P, u, q, ua, qa, n, area, out);
       // block of the neighbour: the own side carries only its cross gradient tangent
       S ub[5], qb[3][5], outb[5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) ub[c] = Dual{u[c].v, 0.0};
+      for (int c = 0; c < 5; ++c) ub[c] = S{u[c].v, R(0)};
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int c = 0; c < 5; ++c) qb[d][c] = Dual{q[d][c].v, qx[(e * 6 + phi) * 15 * NF + (d * 5 + c) * NF + f]};
+        for (int c = 0; c < 5; ++c) qb[d][c] = S{q[d][c].v, qx[(e * 6 + phi) * 15 * NF + (d * 5 + c) * NF + f]};
       face_flux_interior(P, ub, qb, u2, q2, n, area, outb);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) st<S>(fh + ob2 + c * NF, plane_u, -outb[c]);
+      for (int c = 0; c < 5; ++c) st(fh + ob2 + c * NF, plane_u, -outb[c]);
     } else {
       face_flux_interior(P, u, q, u2, q2, n, area, out);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) st<S>(fh + ob2 + c * NF, plane_u, -out[c]);
+      for (int c = 0; c < 5; ++c) st(fh + ob2 + c * NF, plane_u, -out[c]);
     }
   } else if (nb == -DG_BC_WALL) {
     S ubd[5], sg[5];
@@ -435,16 +438,16 @@ __global__ void k_faces(long long E, long long F, Phys P, const int* __restrict_
     flux_dot_n(P, u, q, n, false, out);
   }
 #pragma unroll
-  for (int c = 0; c < 5; ++c) st<S>(fh + ub + c * NF, plane_u, out[c]);
+  for (int c = 0; c < 5; ++c) st(fh + ub + c * NF, plane_u, out[c]);
 }
 
 // --------------------------------------------------------------------------------------------
 // k_volume: pointwise flux and source, projection, lifting of F_hat, B^T -> nodal r (and J v)
 // --------------------------------------------------------------------------------------------
-template <typename S>
-__device__ __forceinline__ void volume_point(const Phys& P, const S u[5], const S q[3][5],
-                                             const double G[9], double Wd, const double acc[3],
-                                             const double* xg, double t, S Fref[3][5], S src[5]) {
+template <typename S, typename R = typename RealOf<S>::type>
+__device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], const S q[3][5],
+                                             const R G[9], R Wd, const R acc[3],
+                                             const R* xg, R t, S Fref[3][5], S src[5]) {
   Prim<S> w;
   primitives(P, u, q, w);
   const S cm = (P.c_mu * w.mu) * w.isr;
@@ -466,15 +469,15 @@ __device__ __forceinline__ void volume_point(const Phys& P, const S u[5], const 
 #pragma unroll
     for (int c = 0; c < 5; ++c) Fref[a][c] = G[a * 3 + 0] * F[c][0] + G[a * 3 + 1] * F[c][1] + G[a * 3 + 2] * F[c][2];
   // source terms
-  const S sr = s_exp(0.5 * u[0]);
+  const S sr = s_exp64(R(0.5) * u[0]);
   const S wxv[3] = {P.omega[1] * w.v[2] - P.omega[2] * w.v[1], P.omega[2] * w.v[0] - P.omega[0] * w.v[2],
                     P.omega[0] * w.v[1] - P.omega[1] * w.v[0]};
-  src[0] = (u[0] - 1.0) * w.div;
+  src[0] = (u[0] - R(1)) * w.div;
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     const S a_m = acc[m] - P.cor * wxv[m];
     const S eg = w.eps[m][0] * q[0][0] + w.eps[m][1] * q[1][0] + w.eps[m][2] * q[2][0];
-    src[1 + m] = sr * a_m + 0.5 * (w.div * u[1 + m]) - (0.5 * P.p_coef) * (u[4] * q[m][0]) + 0.5 * (cm * eg);
+    src[1 + m] = sr * a_m + R(0.5) * (w.div * u[1 + m]) - (R(0.5) * P.p_coef) * (u[4] * q[m][0]) + R(0.5) * (cm * eg);
   }
   const S tg = w.gT[0] * q[0][0] + w.gT[1] * q[1][0] + w.gT[2] * q[2][0];
   S diss = s_zero<S>();
@@ -482,15 +485,15 @@ __device__ __forceinline__ void volume_point(const Phys& P, const S u[5], const 
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int d = 0; d < 3; ++d) diss = diss + w.eps[m][d] * w.gv[m][d];
-  S s4 = (1.5 - P.gamma) * (u[4] * w.div) + 0.5 * (ck * tg) + ((P.c_d / P.cv) * w.mu) * (w.isr * diss);
+  S s4 = (R(1.5) - P.gamma) * (u[4] * w.div) + R(0.5) * (ck * tg) + ((P.c_d / P.cv) * w.mu) * (w.isr * diss);
   if (P.euv) {
-    const double r = sqrt(xg[0] * xg[0] + xg[1] * xg[1] + xg[2] * xg[2]);
-    const double sx = cos(P.euv_omega_t * t), sy = -sin(P.euv_omega_t * t);
-    double cchi = (xg[0] * sx + xg[1] * sy) / r;
-    cchi = fmin(1.0, fmax(-1.0, cchi));
-    const double chi = acos(cchi);
-    const double dz = (r - P.euv_r_peak) * P.euv_inv_w;
-    const double Qh = P.euv_amp * exp(-chi * chi * P.euv_inv2s2) * exp(-0.6931471805599453 * dz * dz);
+    const R r = sqrt(xg[0] * xg[0] + xg[1] * xg[1] + xg[2] * xg[2]);
+    const R sx = cos(P.euv_omega_t * t), sy = -sin(P.euv_omega_t * t);
+    R cchi = (xg[0] * sx + xg[1] * sy) / r;
+    cchi = fmin(R(1), fmax(R(-1), cchi));
+    const R chi = acos(cchi);
+    const R dz = (r - P.euv_r_peak) * P.euv_inv_w;
+    const R Qh = P.euv_amp * s_exp(-chi * chi * P.euv_inv2s2) * s_exp(R(-0.6931471805599453) * dz * dz);
     s4 = s4 + (Qh / P.cv) * w.isr;
   }
   src[4] = s4;
@@ -498,21 +501,22 @@ __device__ __forceinline__ void volume_point(const Phys& P, const S u[5], const 
   for (int c = 0; c < 5; ++c) src[c] = src[c] * Wd;
 }
 
-template <int N, int NC>
-__global__ void k_volume(long long E, const Ops* __restrict__ ops, Phys P, double t,
-                         const double* __restrict__ geo, const double* __restrict__ accg,
-                         const double* __restrict__ xg, const double* __restrict__ ug,
-                         const double* __restrict__ qg, const double* __restrict__ fh,
+template <int N, int NC, typename R>
+__global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
+                         const R* __restrict__ geo, const R* __restrict__ accg,
+                         const R* __restrict__ xg, const R* __restrict__ ug,
+                         const R* __restrict__ qg, const R* __restrict__ fh,
                          double* __restrict__ r, double* __restrict__ jv) {
-  using S = typename std::conditional<NC == 2, Dual, double>::type;
+  using S = typename std::conditional<NC == 2, DualT<R>, R>::type;
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
-  __shared__ SmemOps so;
-  extern __shared__ double smem[];
-  double* sF = smem;                        // [EPB][3][C][NP]
-  double* sH = sF + EPB * 3 * C * NP;       // [EPB][6][C][NF]
-  double* sR = sH + EPB * 6 * C * NF;       // [EPB][C][NP]
-  double* sT = sR + EPB * C * NP;           // [EPB][C][NP]
-  load_ops<N>(ops, so);
+  __shared__ SmemOpsT<R> so;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* smem = reinterpret_cast<R*>(smem_raw);
+  R* sF = smem;                             // [EPB][3][C][NP]
+  R* sH = sF + EPB * 3 * C * NP;            // [EPB][6][C][NF]
+  R* sR = sH + EPB * 6 * C * NF;            // [EPB][C][NP]
+  R* sT = sR + EPB * C * NP;                // [EPB][C][NP]
+  load_ops<N, R>(ops, so);
   const long long e0 = (long long)blockIdx.x * EPB;
   const long long plane_f = E * 30 * NF;
   for (int idx = threadIdx.x; idx < EPB * 30 * NF; idx += blockDim.x) {
@@ -532,18 +536,18 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, Phys P, doubl
     const long long plane_g = E * 5 * NP, plane_q = E * 15 * NP;
     S u[5], q[3][5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) u[c] = ld<S, NC>(ug + e * 5 * NP + c * NP + g, plane_g);
+    for (int c = 0; c < 5; ++c) u[c] = ld<S, NC, R>(ug + e * 5 * NP + c * NP + g, plane_g);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int c = 0; c < 5; ++c) q[d][c] = ld<S, NC>(qg + e * 15 * NP + (d * 5 + c) * NP + g, plane_q);
-    double G[9];
-    const double* gp = geo + e * 10 * NP + g;
+      for (int c = 0; c < 5; ++c) q[d][c] = ld<S, NC, R>(qg + e * 15 * NP + (d * 5 + c) * NP + g, plane_q);
+    R G[9];
+    const R* gp = geo + e * 10 * NP + g;
 #pragma unroll
     for (int k = 0; k < 9; ++k) G[k] = gp[k * NP];
-    const double Wd = gp[9 * NP];
-    const double a3[3] = {accg[e * 3 * NP + g], accg[e * 3 * NP + NP + g], accg[e * 3 * NP + 2 * NP + g]};
-    double x3[3] = {0.0, 0.0, 0.0};
+    const R Wd = gp[9 * NP];
+    const R a3[3] = {accg[e * 3 * NP + g], accg[e * 3 * NP + NP + g], accg[e * 3 * NP + 2 * NP + g]};
+    R x3[3] = {R(0), R(0), R(0)};
     if (P.euv) {
       x3[0] = xg[e * 3 * NP + g];
       x3[1] = xg[e * 3 * NP + NP + g];
@@ -566,29 +570,29 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, Phys P, doubl
   __syncthreads();
   if (active) {
     for (int c = 0; c < C; ++c) {
-      double R;
-      if constexpr (NC == 1) R = srcv[c];
-      else R = (c < 5) ? srcv[c].v : srcv[c - 5].d;
+      R acc;
+      if constexpr (NC == 1) acc = srcv[c];
+      else acc = (c < 5) ? srcv[c].v : srcv[c - 5].d;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) R += line<N, true>(so.D, sF + ((el * 3 + a) * C + c) * NP, g, a);
+      for (int a = 0; a < 3; ++a) acc += line<N, true>(so.D, sF + ((el * 3 + a) * C + c) * NP, g, a);
 #pragma unroll
       for (int phi = 0; phi < 6; ++phi) {
         const int axis = phi >> 1;
-        const double coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
-        R = fma(-coef, sH[((el * 6 + phi) * C + c) * NF + vol_face_point<N>(g, axis)], R);
+        const R coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
+        acc = fma(-coef, sH[((el * 6 + phi) * C + c) * NF + vol_face_point<N>(g, axis)], acc);
       }
-      sR[(el * C + c) * NP + g] = R;
+      sR[(el * C + c) * NP + g] = acc;
     }
   }
   __syncthreads();
-  double* in = sR;
-  double* out = sT;
+  R* in = sR;
+  R* out = sT;
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     if (active)
       for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, true>(so.B, in + (el * C + c) * NP, g, dir);
     __syncthreads();
-    double* tt = in;
+    R* tt = in;
     in = out;
     out = tt;
   }
@@ -596,8 +600,8 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, Phys P, doubl
     const int l = idx / (5 * NP), rem = idx % (5 * NP);
     const long long ee = e0 + l;
     if (ee < E) {
-      if (r) r[ee * 5 * NP + rem] = in[(l * C) * NP + rem];
-      if (NC == 2) jv[ee * 5 * NP + rem] = in[(l * C + 5) * NP + rem];
+      if (r) r[ee * 5 * NP + rem] = (double)in[(l * C) * NP + rem];
+      if (NC == 2) jv[ee * 5 * NP + rem] = (double)in[(l * C + 5) * NP + rem];
     }
   }
 }
@@ -615,7 +619,7 @@ __global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, co
   extern __shared__ double smem[];
   double* b0 = smem;
   double* b1 = smem + C * NP;
-  load_ops<N>(ops, so);
+  load_ops<N, double>(ops, so);
   const long long e = blockIdx.x;
   const int g = threadIdx.x;
   for (int idx = threadIdx.x; idx < C * NP; idx += blockDim.x) b0[idx] = in_g[e * C * NP + idx];
@@ -674,7 +678,7 @@ __global__ void k_geometry(long long E, const Ops* __restrict__ ops, Phys P, int
   double* b0 = smem;           // [3][NP]
   double* b1 = b0 + 3 * NP;    // [3][NP]
   double* J = b1 + 3 * NP;     // [9][NP] J[d][a]
-  load_ops<N>(ops, so);
+  load_ops<N, double>(ops, so);
   if (threadIdx.x < N) w1[threadIdx.x] = ops->w[threadIdx.x];
   const long long e = blockIdx.x;
   const int g = threadIdx.x;
@@ -773,13 +777,19 @@ __global__ void k_geometry(long long E, const Ops* __restrict__ ops, Phys P, int
 // --------------------------------------------------------------------------------------------
 // Driver
 // --------------------------------------------------------------------------------------------
-template <int N, int NC>
+template <int N, int NC, typename R>
 struct Smem {
   static constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
-  static constexpr size_t interp = sizeof(double) * (2 * EPB * C * NP);
-  static constexpr size_t grad = sizeof(double) * (EPB * (C * NP + 6 * C * NF + 18 * NF + 9 * NP + 3 * C * NP));
-  static constexpr size_t volume = sizeof(double) * (EPB * (3 * C * NP + 6 * C * NF + 2 * C * NP));
+  static constexpr size_t interp = sizeof(R) * (2 * EPB * C * NP);
+  static constexpr size_t grad = sizeof(R) * (EPB * (C * NP + 6 * C * NF + 18 * NF + 9 * NP + 3 * C * NP));
+  static constexpr size_t volume = sizeof(R) * (EPB * (3 * C * NP + 6 * C * NF + 2 * C * NP));
 };
+
+template <typename R> inline WorkT<R> work_of(dg_mesh* m);
+template <> inline WorkT<double> work_of<double>(dg_mesh* m) {
+  return WorkT<double>{m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf, m->ws.fh, m->ws.qx, m->geo, m->fgeo, m->acc, m->xg};
+}
+template <> inline WorkT<float> work_of<float>(dg_mesh* m) { return m->w32; }
 
 template <typename K>
 static int set_smem(K kernel, size_t bytes) {
@@ -788,59 +798,63 @@ static int set_smem(K kernel, size_t bytes) {
   return DG_OK;
 }
 
-template <int N, int NC>
+template <int N, int NC, typename R = double>
 static int run_interp(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
-  const size_t sm = Smem<N, NC>::interp;
-  int rc = set_smem(k_interp<N, NC>, sm);
+  const size_t sm = Smem<N, NC, R>::interp;
+  int rc = set_smem(k_interp<N, NC, R>, sm);
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
+  const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_INTERP);
-  k_interp<N, NC><<<blocks, EPB * NP, sm, s>>>(u, v, m->E, m->d_ops, m->ws.ug, m->ws.uf);
+  k_interp<N, NC, R><<<blocks, EPB * NP, sm, s>>>(u, v, m->E, m->d_ops, w.ug, w.uf);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_interp");
   return DG_OK;
 }
 
-template <int N, int NC, bool BLK = false>
+template <int N, int NC, bool BLK = false, typename R = double>
 static int run_grad(dg_mesh* m, cudaStream_t s) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
-  const size_t sm = Smem<N, NC>::grad;
-  int rc = set_smem(k_grad<N, NC, BLK>, sm);
+  const size_t sm = Smem<N, NC, R>::grad;
+  int rc = set_smem(k_grad<N, NC, BLK, R>, sm);
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
+  const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_GRAD);
-  k_grad<N, NC, BLK><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, m->phys, m->geo, m->fgeo, m->nbr, m->nbr_fo,
-                                                   m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf, m->ws.qx);
+  k_grad<N, NC, BLK, R><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), w.geo, w.fgeo, m->nbr,
+                                                      m->nbr_fo, w.ug, w.uf, w.qg, w.qf, w.qx);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_grad");
   return DG_OK;
 }
 
-template <int N, int NC, bool BLK = false>
+template <int N, int NC, bool BLK = false, typename R = double>
 static int run_faces(dg_mesh* m, cudaStream_t s) {
   constexpr int NF = Shape<N>::NF;
   const long long work = m->nfaces * NF;
   const int threads = 128;
   const unsigned blocks = (unsigned)((work + threads - 1) / threads);
+  const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_FACES);
-  k_faces<N, NC, BLK><<<blocks, threads, 0, s>>>(m->E, m->nfaces, m->phys, m->face_e, m->face_f, m->nbr,
-                                                  m->nbr_fo, m->fgeo, m->ws.uf, m->ws.qf, m->ws.qx, m->ws.fh);
+  k_faces<N, NC, BLK, R><<<blocks, threads, 0, s>>>(m->E, m->nfaces, phys_as<R>(m->phys), m->face_e, m->face_f,
+                                                     m->nbr, m->nbr_fo, w.fgeo, w.uf, w.qf, w.qx, w.fh);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_faces");
   return DG_OK;
 }
 
-template <int N, int NC>
+template <int N, int NC, typename R = double>
 static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t s) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
-  const size_t sm = Smem<N, NC>::volume;
-  int rc = set_smem(k_volume<N, NC>, sm);
+  const size_t sm = Smem<N, NC, R>::volume;
+  int rc = set_smem(k_volume<N, NC, R>, sm);
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
+  const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_VOLUME);
-  k_volume<N, NC><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, m->phys, t, m->geo, m->acc, m->xg, m->ws.ug,
-                                                m->ws.qg, m->ws.fh, r, jv);
+  k_volume<N, NC, R><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), (R)t, w.geo, w.acc, w.xg,
+                                                   w.ug, w.qg, w.fh, r, jv);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_volume");
   return DG_OK;
@@ -863,32 +877,51 @@ int Driver<N>::geometry(dg_mesh* m, cudaStream_t s) {
 }
 
 template <int N>
-int Driver<N>::gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
-  int rc = v ? run_interp<N, 2>(m, u, v, s) : run_interp<N, 1>(m, u, nullptr, s);
+template <typename R>
+int Driver<N>::gradient_p(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
+  int rc = v ? run_interp<N, 2, R>(m, u, v, s) : run_interp<N, 1, R>(m, u, nullptr, s);
   if (rc) return rc;
-  return v ? run_grad<N, 2>(m, s) : run_grad<N, 1>(m, s);
+  return v ? run_grad<N, 2, false, R>(m, s) : run_grad<N, 1, false, R>(m, s);
+}
+
+template <int N>
+template <typename R>
+int Driver<N>::residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s) {
+  int rc = tangent ? run_faces<N, 2, false, R>(m, s) : run_faces<N, 1, false, R>(m, s);
+  if (rc) return rc;
+  return tangent ? run_volume<N, 2, R>(m, t, r, jv, s) : run_volume<N, 1, R>(m, t, r, nullptr, s);
+}
+
+template <int N>
+int Driver<N>::gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32) {
+  return f32 ? gradient_p<float>(m, u, v, s) : gradient_p<double>(m, u, v, s);
 }
 
 template <int N>
 int Driver<N>::residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
-                        bool tangent, cudaStream_t s) {
+                        bool tangent, cudaStream_t s, bool f32) {
   (void)u;
   (void)v;
-  int rc = tangent ? run_faces<N, 2>(m, s) : run_faces<N, 1>(m, s);
+  return f32 ? residual_p<float>(m, t, r, jv, tangent, s) : residual_p<double>(m, t, r, jv, tangent, s);
+}
+
+template <int N>
+template <typename R>
+int Driver<N>::jv_blockdiag_p(dg_mesh* m, const double* u, const double* probe, double t, double* jv,
+                              cudaStream_t s) {
+  int rc = run_interp<N, 2, R>(m, u, probe, s);
   if (rc) return rc;
-  return tangent ? run_volume<N, 2>(m, t, r, jv, s) : run_volume<N, 1>(m, t, r, nullptr, s);
+  rc = run_grad<N, 2, true, R>(m, s);
+  if (rc) return rc;
+  rc = run_faces<N, 2, true, R>(m, s);
+  if (rc) return rc;
+  return run_volume<N, 2, R>(m, t, nullptr, jv, s);
 }
 
 template <int N>
 int Driver<N>::jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv,
-                            cudaStream_t s) {
-  int rc = run_interp<N, 2>(m, u, probe, s);
-  if (rc) return rc;
-  rc = run_grad<N, 2, true>(m, s);
-  if (rc) return rc;
-  rc = run_faces<N, 2, true>(m, s);
-  if (rc) return rc;
-  return run_volume<N, 2>(m, t, nullptr, jv, s);
+                            cudaStream_t s, bool f32) {
+  return f32 ? jv_blockdiag_p<float>(m, u, probe, t, jv, s) : jv_blockdiag_p<double>(m, u, probe, t, jv, s);
 }
 
 template <int N>

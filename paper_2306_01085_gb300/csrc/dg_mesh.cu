@@ -30,12 +30,12 @@ int fail(int code, const std::string& msg) {
   }
 
 static int drv_geometry(dg_mesh* m, cudaStream_t s) { DG_DISPATCH(m, geometry(m, s)); }
-static int drv_gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
-  DG_DISPATCH(m, gradient(m, u, v, s));
+static int drv_gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32 = false) {
+  DG_DISPATCH(m, gradient(m, u, v, s, f32));
 }
 static int drv_residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
-                        bool tan, cudaStream_t s) {
-  DG_DISPATCH(m, residual(m, u, v, t, r, jv, tan, s));
+                        bool tan, cudaStream_t s, bool f32 = false) {
+  DG_DISPATCH(m, residual(m, u, v, t, r, jv, tan, s, f32));
 }
 static int drv_q_to_nodal(dg_mesh* m, double* q, cudaStream_t s) { DG_DISPATCH(m, q_to_nodal(m, q, s)); }
 static int drv_q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) { DG_DISPATCH(m, q_from_nodal(m, q, s)); }
@@ -278,6 +278,7 @@ static void prof_release(dg_mesh* m) {
 static void free_mesh(dg_mesh* m) {
   prof_release(m);
   dg_solver_release(m);
+  if (m->w32_base) cudaFree(m->w32_base);
   void* ptrs[] = {m->d_ops, m->x, m->geo, m->acc, m->xg, m->fgeo, m->nbr, m->nbr_fo, m->face_e, m->face_f,
                   m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf, m->ws.fh, m->ws.tmp, m->ws.red, m->ws.qx};
   for (void* p : ptrs)
@@ -301,6 +302,45 @@ static int dalloc(T** p, size_t count) {
 using namespace dg;
 
 extern "C" const char* dg_last_error(void) { return g_last_error.c_str(); }
+
+namespace dg {
+
+__global__ void k_to_f32(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+int ensure_f32(dg_mesh* m) {
+  if (m->w32_base) return DG_OK;
+  const long long E = m->E, NP = m->np, NF = m->nf;
+  const long long sizes[10] = {2 * E * 5 * NP, 2 * E * 30 * NF, 2 * E * 15 * NP, 2 * E * 90 * NF, 2 * E * 30 * NF,
+                               E * 90 * NF,    E * 10 * NP,     E * 24 * NF,     E * 3 * NP,      E * 3 * NP};
+  long long total = 0;
+  for (long long z : sizes) total += (z + 63) / 64 * 64;
+  cudaError_t err = cudaMalloc(&m->w32_base, sizeof(float) * (size_t)total);
+  if (err != cudaSuccess) {
+    m->w32_base = nullptr;
+    return fail(DG_ENOMEM, std::string("FP32 workspace: ") + cudaGetErrorString(err));
+  }
+  float* p[10];
+  long long off = 0;
+  for (int k = 0; k < 10; ++k) {
+    p[k] = m->w32_base + off;
+    off += (sizes[k] + 63) / 64 * 64;
+  }
+  m->w32 = WorkT<float>{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9]};
+  const double* src[4] = {m->geo, m->fgeo, m->acc, m->xg};
+  for (int k = 0; k < 4; ++k) {
+    k_to_f32<<<1024, 256>>>(sizes[6 + k], src[k], p[6 + k]);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(DG_ECUDA, std::string("k_to_f32: ") + cudaGetErrorString(err));
+  }
+  err = cudaDeviceSynchronize();
+  if (err != cudaSuccess) return fail(DG_ECUDA, std::string("FP32 geometry: ") + cudaGetErrorString(err));
+  return DG_OK;
+}
+
+}  // namespace dg
 
 extern "C" int dg_mesh_create(const dg_mesh_desc* desc, const double* nodes, dg_mesh** out) {
   if (!desc || !out) return fail(DG_EINVAL, "dg_mesh_create: null argument");
@@ -613,4 +653,25 @@ extern "C" int dg_profile_stop(dg_mesh* mesh, int32_t n_kinds, double* ms, int32
   if (total) *total = p.launches;
   prof_release(mesh);
   return rc;
+}
+
+extern "C" int dg_residual_f32(dg_mesh* mesh, const double* u, double t, double* r, void* stream) {
+  if (!mesh || !u || !r) return fail(DG_EINVAL, "dg_residual_f32: null argument");
+  int rc = ensure_f32(mesh);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = drv_gradient(mesh, u, nullptr, s, true);
+  if (rc) return rc;
+  return drv_residual(mesh, u, nullptr, t, r, nullptr, false, s, true);
+}
+
+extern "C" int dg_jvp_f32(dg_mesh* mesh, const double* u, const double* v, double t, double* jv, double* r_out,
+                          void* stream) {
+  if (!mesh || !u || !v || !jv) return fail(DG_EINVAL, "dg_jvp_f32: null argument");
+  int rc = ensure_f32(mesh);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = drv_gradient(mesh, u, v, s, true);
+  if (rc) return rc;
+  return drv_residual(mesh, u, v, t, r_out, jv, true, s, true);
 }

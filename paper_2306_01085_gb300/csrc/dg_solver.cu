@@ -385,12 +385,15 @@ static unsigned grid_for(long long n) {
 }
 
 // J_G v = M v - c J_r(U) v
-static int stage_matvec(dg_mesh* m, Solver* S, const double* U, double t, double c, int jv_mode,
+static int stage_matvec(dg_mesh* m, Solver* S, const double* U, double t, double c, int jv_mode, int jv_prec,
                         const double* v, double* out, cudaStream_t s) {
   double* mv = S->v(VTMP);
   int rc = dg_mass_apply(m, v, mv, s);
   if (rc) return rc;
-  rc = dg_jvp(m, U, v, t, jv_mode, 0.0, out, nullptr, s);
+  if (jv_prec == DG_PREC_F32 && jv_mode == DG_JV_EXACT)
+    rc = dg_jvp_f32(m, U, v, t, out, nullptr, s);
+  else
+    rc = dg_jvp(m, U, v, t, jv_mode, 0.0, out, nullptr, s);
   if (rc) return rc;
   prof_begin(m, s, KK_BLAS);
   k_lincomb<<<grid_for(S->n), 256, 0, s>>>(S->n, 1.0, mv, -c, out, 0.0, nullptr, out);
@@ -416,9 +419,15 @@ static int norm2(dg_mesh* m, Solver* S, const double* x, double* out, cudaStream
 // preconditioner
 // ------------------------------------------------------------------------------------------
 // exact diagonal blocks of J_G = M - c J_r(U), column j of every element per sweep, into dest
-static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double c, float* dest, cudaStream_t s) {
+static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double c, float* dest, cudaStream_t s,
+                       bool f32 = false) {
   int rc = ensure_blocks(m, S);
   if (rc) return rc;
+  if (f32) {
+    rc = ensure_f32(m);
+    if (rc) return rc;
+    if (!m->w32.qx) return fail(DG_EINVAL, "FP32 workspace without cross traces");
+  }
   const int nb = 5 * m->np;
   double* jv = S->v(VW);
   double* mv = S->v(VTMP);
@@ -426,7 +435,7 @@ static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double 
     prof_begin(m, s, KK_BLAS);
     k_probe<<<grid_for(S->n), 256, 0, s>>>(m->E, nb, j, S->probe);
     prof_end(m, s);
-    DG_DISPATCH_S(m, jv_blockdiag(m, U, S->probe, t, jv, s));
+    DG_DISPATCH_S(m, jv_blockdiag(m, U, S->probe, t, jv, s, f32));
     if (rc) return rc;
     rc = dg_mass_apply(m, S->probe, mv, s);
     if (rc) return rc;
@@ -438,12 +447,12 @@ static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double 
   return DG_OK;
 }
 
-static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, cudaStream_t s) {
+static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, cudaStream_t s, bool f32 = false) {
   int rc = ensure_blocks(m, S);
   if (rc) return rc;
   const int nb = 5 * m->np;
   DG_CUDA_TRY(cudaMemsetAsync(S->info, 0, sizeof(int), s));
-  rc = bj_assemble(m, S, U, t, c, S->blocks, s);
+  rc = bj_assemble(m, S, U, t, c, S->blocks, s, f32);
   if (rc) return rc;
   prof_begin(m, s, KK_LU);
   k_lu<<<(unsigned)m->E, 256, 0, s>>>(m->E, nb, S->blocks, S->piv, S->info);
@@ -497,7 +506,7 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
     if (cycle == 0) {
       DG_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     } else {
-      rc = stage_matvec(m, S, U, t, c, o.jv_mode, x, w, s);
+      rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, x, w, s);
       if (rc) return rc;
       k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, b, -1.0, w, 0.0, nullptr, r);
       DG_LAUNCH_CHECK("k_lincomb");
@@ -516,7 +525,7 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
     for (int k = 0; k < R; ++k) {
       rc = precond_apply(m, S, o.precond, V + (long long)k * n, z, s);
       if (rc) return rc;
-      rc = stage_matvec(m, S, U, t, c, o.jv_mode, z, w, s);
+      rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, z, w, s);
       if (rc) return rc;
       // classical Gram-Schmidt twice; h and the norm stay on the device until one read-back
       prof_begin(m, s, KK_BLAS);
@@ -644,7 +653,7 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
   };
   if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_STEP) {
     const auto p0 = std::chrono::steady_clock::now();
-    rc = bj_setup(mesh, S, un, t + c[0] * dt, dt * A[0][0], s);
+    rc = bj_setup(mesh, S, un, t + c[0] * dt, dt * A[0][0], s, o.jv_prec == DG_PREC_F32);
     st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
     if (rc) return finish(rc);
   }
@@ -658,7 +667,7 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
     DG_LAUNCH_CHECK("k_lincomb");
     if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_STAGE) {
       const auto p0 = std::chrono::steady_clock::now();
-      rc = bj_setup(mesh, S, U, ti, ci, s);
+      rc = bj_setup(mesh, S, U, ti, ci, s, o.jv_prec == DG_PREC_F32);
       st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
       if (rc) return finish(rc);
     }
@@ -688,7 +697,7 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
       if (it == o.max_newton) break;
       if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_NEWTON) {
         const auto p0 = std::chrono::steady_clock::now();
-        rc = bj_setup(mesh, S, U, ti, ci, s);
+        rc = bj_setup(mesh, S, U, ti, ci, s, o.jv_prec == DG_PREC_F32);
         st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
         if (rc) return finish(rc);
       }

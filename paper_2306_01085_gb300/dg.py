@@ -39,7 +39,7 @@ class DgSolverOpts(ctypes.Structure):
     _fields_ = [
         ("stages", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
         ("max_newton", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_refresh", ctypes.c_int32),
-        ("jv_mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("newton_rtol", ctypes.c_double),
+        ("jv_mode", ctypes.c_int32), ("jv_prec", ctypes.c_int32), ("newton_rtol", ctypes.c_double),
         ("gmres_rtol", ctypes.c_double), ("abs_floor", ctypes.c_double),
     ]
 
@@ -90,6 +90,8 @@ def lib():
     L.dg_kernel_name.argtypes = [i32]
     L.dg_kernel_name.restype = ctypes.c_char_p
     L.dg_probe_fp64.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    L.dg_residual_f32.argtypes = [vp, dp, d, dp, vp]
+    L.dg_jvp_f32.argtypes = [vp, dp, dp, d, dp, dp, vp]
     L.dg_solver_opts_default.argtypes = [ctypes.POINTER(DgSolverOpts)]
     L.dg_solver_opts_default.restype = None
     L.dg_dirk_tableau.argtypes = [i32, dp, dp]
@@ -243,6 +245,8 @@ def solver_opts(**kw):
             v = REFRESH[v]
         if k == "jv_mode" and isinstance(v, str):
             v = DG_JV_EXACT if v == "exact" else DG_JV_FD
+        if k == "jv_prec" and isinstance(v, str):
+            v = 1 if v == "f32" else 0
         setattr(o, k, v)
     return o
 
@@ -299,3 +303,22 @@ Mesh.implicit_step = _mesh_implicit_step
 Mesh.precond_setup = _mesh_precond_setup
 Mesh.precond_apply = _mesh_precond_apply
 Mesh.block_assemble = _mesh_block_assemble
+
+
+def _mesh_residual_f32(self, u, t=0.0, out=None):
+    """FP32 residual (FP64 in and out; exp(log rho) in FP64)."""
+    r = out if out is not None else self.empty()
+    _check(lib().dg_residual_f32(self._h, _ptr(u, self.u_shape, "u"), float(t), _ptr(r, self.u_shape, "r"), _stream()))
+    return r
+
+
+def _mesh_jvp_f32(self, u, v, t=0.0, out=None, r_out=None):
+    """FP32 exact Jv (and residual when r_out is given)."""
+    jv = out if out is not None else self.empty()
+    _check(lib().dg_jvp_f32(self._h, _ptr(u, self.u_shape, "u"), _ptr(v, self.u_shape, "v"), float(t),
+                            _ptr(jv, self.u_shape, "jv"), _ptr(r_out, self.u_shape, "r_out"), _stream()))
+    return jv
+
+
+Mesh.residual_f32 = _mesh_residual_f32
+Mesh.jvp_f32 = _mesh_jvp_f32
