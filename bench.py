@@ -44,8 +44,10 @@ def parse():
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--implicit", action="store_true",
                     help="time the implicit DIRK step variants instead (configs shell32x16_p2_euv, shell48x16_p3_euv)")
-    ap.add_argument("--variants", default="plain_bj,mixed_bj,plain_none",
+    ap.add_argument("--variants", default="plain_bj,mixed_bj,mixed_mlp,plain_none",
                     help="comma list for --implicit: plain_bj, mixed_bj, plain_none, mixed_mlp")
+    ap.add_argument("--mlp-steps", type=int, default=2, help="plain steps whose blocks train the network")
+    ap.add_argument("--mlp-epochs", type=int, default=20)
     return ap.parse_args()
 
 
@@ -327,6 +329,8 @@ def main_implicit(args):
     plain_bj:   FP64 residual and exact FP64 Jv, block-Jacobi on exact blocks (FP32 LU)
     mixed_bj:   FP64 residual, FP32 inner Jv and FP32-assembled blocks (FP32 LU)
     plain_none: FP64 unpreconditioned GMRES(30)
+    mixed_mlp:  mixed precision with the learned diagonal + low-rank preconditioner, trained first on
+                the exact blocks of --mlp-steps plain steps (training time reported separately)
     Every variant starts from the same state; the final states are compared with plain_bj.
     """
     import numpy as np
@@ -347,18 +351,47 @@ def main_implicit(args):
         "mixed_bj": dict(precond="bj", jv_prec="f32"),
         "plain_none": dict(precond="none", jv_prec="f64"),
     }
+    variants["mixed_mlp"] = dict(precond="mlp", jv_prec="f32")
     results, finals = {}, {}
+    training = None
+    if "mixed_mlp" in args.variants.split(","):
+        # harvest exact blocks from plain steps (each step's initial state, coefficient dt a_ii),
+        # then train the network with the library's own kernels
+        gamma = float(DG.dirk_tableau(3)[0][0, 0])
+        n_harvest = max(1, args.mlp_steps)
+        mesh.mlp_init(hidden=256, rank=16, max_samples=n_harvest * mesh.n_elem, seed=11)
+        u = u0.clone()
+        t_h = time.perf_counter()
+        for k in range(n_harvest):
+            mesh.mlp_harvest(u, k * dt, dt * gamma, stride=1)
+            mesh.implicit_step(u, k * dt, dt, stages=3, precond="bj", jv_prec="f32")
+        t_h = time.perf_counter() - t_h
+        torch.cuda.synchronize()
+        t_t = time.perf_counter()
+        first, last = mesh.mlp_train(epochs=args.mlp_epochs, batch=1024, lr=1e-3)
+        torch.cuda.synchronize()
+        training = {"samples": mesh.mlp_sizes()["n_samples"], "harvest_steps": n_harvest,
+                    "harvest_s": round(t_h, 2), "train_s": round(time.perf_counter() - t_t, 2),
+                    "epochs": args.mlp_epochs, "loss_first_epoch": first, "loss_last_epoch": last,
+                    "params": mesh.mlp_sizes()["n_params"]}
     for name in args.variants.split(","):
         kw = variants[name]
         u = u0.clone()
         steps = []
         rc = 0
+        kernels = None
         for k in range(args.steps):
+            last = k == args.steps - 1
+            if last:
+                mesh.profile_start(capacity=200000)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st = mesh.implicit_step(u, k * dt, dt, stages=3, check=False, **kw)
             torch.cuda.synchronize()
             st["wall_s"] = time.perf_counter() - t0
+            if last:
+                prof, _ = mesh.profile_stop()
+                kernels = {kn: {"ms": round(v[0], 2), "launches": v[1]} for kn, v in prof.items()}
             steps.append(st)
             rc = st["rc"]
             if rc != 0:
@@ -370,7 +403,8 @@ def main_implicit(args):
                          "wall_s_per_step": [round(st["wall_s"], 4) for st in steps],
                          "precond_s_per_step": [round(st["precond_ms"] / 1e3, 4) for st in steps],
                          "newton_per_step": newton, "gmres_per_step": gmres,
-                         "gmres_per_newton": round(sum(gmres) / max(1, sum(newton)), 2)}
+                         "gmres_per_newton": round(sum(gmres) / max(1, sum(newton)), 2),
+                         "kernels_last_step": kernels}
     ref = finals.get("plain_bj")
     if ref is not None:
         du = np.abs(ref - u0.cpu().numpy()).max(axis=(0, 2))
@@ -379,9 +413,11 @@ def main_implicit(args):
                 results[name]["final_diff_rel_to_change"] = (np.abs(fin - ref).max(axis=(0, 2)) / du).tolist()
     base = results.get("plain_bj", {}).get("wall_s_per_step")
     out = {"metric": "implicit DIRK(3,3) step wall time at Newton 1e-8", "unit": "s/step", "config": config,
-           "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "dt_s": 60.0, "steps": args.steps, "variants": results}
-    if base and results.get("mixed_bj", {}).get("rc") == 0:
-        out["speedup_mixed_vs_plain"] = round(np.mean(base) / np.mean(results["mixed_bj"]["wall_s_per_step"]), 3)
+           "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "dt_s": 60.0, "steps": args.steps, "variants": results,
+           "mlp_training": training}
+    for name in ("mixed_bj", "mixed_mlp"):
+        if base and results.get(name, {}).get("rc") == 0:
+            out[f"speedup_{name}_vs_plain_bj"] = round(np.mean(base) / np.mean(results[name]["wall_s_per_step"]), 3)
     print(json.dumps(out), flush=True)
     mesh.close()
 

@@ -167,7 +167,7 @@ int dg_residual_static(dg_mesh* mesh, const double* u, double t, double* r, void
  * Implicit time step (Sec. 3.1-3.2): DIRK stages solved by Newton-GMRES
  * -------------------------------------------------------------------------------------------- */
 #define DG_PC_NONE 0         /* no preconditioner */
-#define DG_PC_BJ   1         /* exact element diagonal blocks of J_G, FP32 LU (block-Jacobi) */
+#define DG_PC_BJ   1         /* exact element diagonal blocks of J_G, FP32 inverses (block-Jacobi) */
 #define DG_PC_MLP  2         /* learned diagonal + low-rank inverse per element */
 
 #define DG_REFRESH_STEP   0  /* build the preconditioner once per step, at u_n */
@@ -225,10 +225,13 @@ int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, const dg_sol
                      dg_step_stats* stats, void* stream);
 
 /*
- * Build a preconditioner of J_G = M - dt_aii J_r(u) at state u and time t.
+ * Build a preconditioner of J_G = M - dt_aii J_r(u) at state u and time t (DG_PC_MLP: network
+ * inference for every element; see dg_mlp_init).
  * DG_PC_BJ: the exact diagonal block of every element (including the path through the
- * neighbours' LDG gradients) is computed column by column by block-diagonal tangent sweeps, then
- * factored by FP32 LU with partial pivoting. Synchronises the stream. DG_ENAN on a zero pivot.
+ * neighbours' LDG gradients) is computed column by column by block-diagonal tangent sweeps and
+ * inverted in place in FP32 by Gauss-Jordan elimination with partial pivoting, so that applying
+ * the preconditioner is one coalesced dense product per element. Synchronises the stream.
+ * DG_ENAN on a zero pivot.
  * The blocks are exact when no two faces of an element border the same neighbour (every shell;
  * boxes with at least 3 elements along each periodic direction); otherwise the gradient lifted
  * from one shared face into the other is left out and the block is an approximation.
@@ -242,6 +245,39 @@ int dg_precond_apply(dg_mesh* mesh, int32_t kind, const double* x, double* y, vo
  * caller device buffer out, FP32 [n_elem][5 n_p][5 n_p], each block column-major (out[e][j][i] =
  * row i, column j; rows and columns in the element's [var][node] order). Stream-ordered. */
 int dg_block_assemble(dg_mesh* mesh, const double* u, double t, double dt_aii, float* out, void* stream);
+
+/* ----------------------------------------------------------------------------------------------
+ * Learned element preconditioner (DG_PC_MLP; the paper has none, Sec. 3.2 uses a reduced basis).
+ * Per element, features x (nodal varrho - mean, v, T/mean(T) - 1, mean(varrho)/10, log mean(T),
+ * log(dt a_ii), log of the three element extents; 5 n_p + 6 values) go through a two-hidden-layer
+ * SiLU network to D = 1 + o[:n], U, V (n x rank, row-major), n = 5 n_p, and the preconditioner is
+ * P = S^{-1/2} (diag(D) + U V^T) S^{-1/2} with S the diagonal of the element mass matrix. Training
+ * minimises mean || S^{-1/2} B S^{-1/2} (diag(D) + U V^T) - I ||_F^2 / n (P as a right inverse, as
+ * GMRES applies it) over harvested exact blocks B of J_G with Adam; forward, backward and optimiser
+ * run in the library's own FP32 kernels.
+ * Supported for p <= 3.
+ * -------------------------------------------------------------------------------------------- */
+/* Create the network (weights from SplitMix64 with seed) and room for max_samples samples. */
+int dg_mlp_init(dg_mesh* mesh, int32_t hidden, int32_t rank, int64_t max_samples, uint64_t seed);
+/* Sizes: parameters, inputs, outputs, harvested samples (any pointer may be NULL). */
+int dg_mlp_sizes(dg_mesh* mesh, int64_t* n_params, int32_t* n_in, int32_t* n_out, int64_t* n_samples);
+/* Copy the FP32 parameters (W1 [hidden][n_in], b1, W2 [hidden][hidden], b2, W3 [n_out][hidden], b3)
+ * to out and/or replace them from in (device buffers; either may be NULL). */
+int dg_mlp_params(dg_mesh* mesh, float* out, const float* in, void* stream);
+/* Features [n_elem][n_in] and mass diagonals [n_elem][n_p] of state u (device outputs, may be NULL). */
+int dg_mlp_features(dg_mesh* mesh, const double* u, double dt_aii, float* feat, float* sdiag, void* stream);
+/* Assemble the exact blocks of J_G at (u, t, dt_aii) and append every stride-th element's
+ * (features, scaled block) to the training set (until full). Synchronises the stream. */
+int dg_mlp_harvest(dg_mesh* mesh, const double* u, double t, double dt_aii, int32_t stride, int64_t* n_samples,
+                   void* stream);
+/* Loss and parameter gradient of nb samples given on the device (X [nb][n_in], scaled blocks
+ * [nb][n][n] row-major); grad (device, n_params floats) may be NULL. Synchronises the stream. */
+int dg_mlp_loss_grad(dg_mesh* mesh, const float* X, const float* Bs, int32_t nb, double* loss, float* grad,
+                     void* stream);
+/* Adam over the harvested set, mini-batches of `batch`, `epochs` passes; mean loss of the first
+ * and the last pass. */
+int dg_mlp_train(dg_mesh* mesh, int32_t epochs, int32_t batch, double lr, double* loss_first, double* loss_last,
+                 void* stream);
 
 /*
  * Tracing. dg_profile_start makes every kernel the library launches for this mesh record a pair

@@ -77,6 +77,7 @@ enum KernelKind {
   KK_INTERP = 0, KK_GRAD, KK_FACES, KK_VOLUME, KK_TENSOR, KK_BLAS, KK_GEOMETRY, KK_LU, KK_PRECOND, KK_COUNT
 };
 struct Solver;
+struct Mlp;
 template <typename R>
 struct WorkT {
   R *ug, *uf, *qg, *qf, *fh, *qx;
@@ -113,11 +114,16 @@ struct dg_mesh {
   dg::Solver* solver = nullptr;   // implicit-step storage, created on first use
   dg::WorkT<float> w32 = {};        // FP32 workspace and geometry, created on first FP32 call
   float* w32_base = nullptr;
+  dg::Mlp* mlp = nullptr;           // learned preconditioner, created by dg_mlp_init
 };
+
+void dg_mlp_release(dg_mesh* m);
 
 namespace dg {
 int ensure_f32(dg_mesh* m);       // allocate and fill the FP32 workspace and geometry
 }
+int mlp_setup(dg_mesh* mesh, const double* u, double dt_aii, cudaStream_t s);
+int mlp_apply(dg_mesh* mesh, const double* x, double* y, cudaStream_t s);
 
 void dg_solver_release(dg_mesh* m);
 

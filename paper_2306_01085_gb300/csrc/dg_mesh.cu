@@ -278,6 +278,7 @@ static void prof_release(dg_mesh* m) {
 static void free_mesh(dg_mesh* m) {
   prof_release(m);
   dg_solver_release(m);
+  dg_mlp_release(m);
   if (m->w32_base) cudaFree(m->w32_base);
   void* ptrs[] = {m->d_ops, m->x, m->geo, m->acc, m->xg, m->fgeo, m->nbr, m->nbr_fo, m->face_e, m->face_f,
                   m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf, m->ws.fh, m->ws.tmp, m->ws.red, m->ws.qx};
@@ -601,7 +602,7 @@ extern "C" int dg_mass_apply(dg_mesh* mesh, const double* v, double* mv, void* s
 }
 
 static const char* kKernelNames[KK_COUNT] = {"k_interp", "k_grad", "k_faces", "k_volume", "k_tensor", "k_blas",
-                                             "k_geometry", "k_lu", "k_lu_solve"};
+                                             "k_geometry", "k_lu", "k_precond_apply"};
 
 extern "C" const char* dg_kernel_name(int32_t kind) {
   return (kind >= 0 && kind < KK_COUNT) ? kKernelNames[kind] : "";

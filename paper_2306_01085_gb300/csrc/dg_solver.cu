@@ -5,7 +5,8 @@
 // J_G = M - dt a_ii J_r is solved by right-preconditioned restarted GMRES whose only operator is
 // the Jacobian-vector product. Arnoldi (classical Gram-Schmidt applied twice), the Hessenberg
 // least-squares problem and every norm are FP64. The block-Jacobi preconditioner factors the exact
-// element diagonal blocks of J_G in FP32 (batched LU with partial pivoting).
+// element diagonal blocks of J_G in FP32 and applies their explicit inverses (batched in-place
+// Gauss-Jordan with partial pivoting).
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -204,8 +205,16 @@ __global__ void k_scatter_col(long long E, int n, int j, double c, const double*
   }
 }
 
-// in-place LU with partial pivoting of one n x n column-major block per CTA
-__global__ void k_lu(long long E, int n, float* __restrict__ blocks, int* __restrict__ piv, int* __restrict__ info) {
+// in-place Gauss-Jordan inversion with partial pivoting of one n x n column-major block per CTA
+// (A[j n + i] = row i, column j). Step k: pick the pivot row in column k, interchange it with row
+// k, scale row k by the reciprocal pivot (the pivot position takes the reciprocal itself) and
+// eliminate column k from every other row (that column takes -a_ik / pivot). After n steps the
+// columns are interchanged back in reverse pivot order, leaving A^{-1}.
+__global__ void k_gj_inverse(long long E, int n, float* __restrict__ blocks, int* __restrict__ piv,
+                             int* __restrict__ info) {
+  extern __shared__ float sfr[];
+  float* f = sfr;        // column k before the step
+  float* r = sfr + n;    // scaled row k
   const long long e = blockIdx.x;
   float* A = blocks + e * (long long)n * n;
   int* pv = piv + e * n;
@@ -241,56 +250,49 @@ __global__ void k_lu(long long E, int n, float* __restrict__ blocks, int* __rest
     __syncthreads();
     const int p = p_sh;
     if (p != k)
-      for (int col = threadIdx.x; col < n; col += blockDim.x) {
-        float* ac = A + (long long)col * n;
-        const float t = ac[k];
-        ac[k] = ac[p];
-        ac[p] = t;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        float* col = A + (long long)j * n;
+        const float t = col[k];
+        col[k] = col[p];
+        col[p] = t;
       }
     __syncthreads();
-    const float inv = 1.0f / A[(long long)k * n + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(long long)k * n + i] *= inv;
+    const float pinv = 1.0f / A[(long long)k * n + k];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = A[(long long)k * n + i];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) r[j] = (j == k ? 1.0f : A[(long long)j * n + k]) * pinv;
     __syncthreads();
-    const int m = n - k - 1;
-    for (long long t = threadIdx.x; t < (long long)m * m; t += blockDim.x) {
-      const int jj = k + 1 + (int)(t / m), ii = k + 1 + (int)(t % m);
-      A[(long long)jj * n + ii] -= A[(long long)k * n + ii] * A[(long long)jj * n + k];
+    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
+      const int j = (int)(t / n), i = (int)(t % n);
+      if (i == k) A[t] = r[j];
+      else A[t] = (j == k ? 0.0f : A[t]) - f[i] * r[j];
     }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = pv[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float t = A[(long long)k * n + i];
+        A[(long long)k * n + i] = A[(long long)p * n + i];
+        A[(long long)p * n + i] = t;
+      }
     __syncthreads();
   }
 }
 
-// y = B^{-1} x per element with the LU factors (FP32 arithmetic, FP64 in and out)
-__global__ void k_lu_solve(long long E, int n, const float* __restrict__ blocks, const int* __restrict__ piv,
-                           const double* __restrict__ x, double* __restrict__ y) {
+// y = B^{-1} x per element with the explicit FP32 inverse (column-major): coalesced over rows
+__global__ void k_inv_apply(long long E, int n, const float* __restrict__ inv, const double* __restrict__ x,
+                            double* __restrict__ y) {
   extern __shared__ float sx[];
   const long long e = blockIdx.x;
-  const float* A = blocks + e * (long long)n * n;
+  const float* A = inv + e * (long long)n * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) sx[i] = (float)x[e * n + i];
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int k = 0; k < n; ++k) {
-      const int p = piv[e * n + k];
-      if (p != k) {
-        const float t = sx[k];
-        sx[k] = sx[p];
-        sx[p] = t;
-      }
-    }
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    const float xk = sx[k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) sx[i] -= A[(long long)k * n + i] * xk;
-    __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float acc = 0.f;
+    for (int j = 0; j < n; ++j) acc = fmaf(A[(long long)j * n + i], sx[j], acc);
+    y[e * n + i] = (double)acc;
   }
-  for (int k = n - 1; k >= 0; --k) {
-    if (threadIdx.x == 0) sx[k] /= A[(long long)k * n + k];
-    __syncthreads();
-    const float xk = sx[k];
-    for (int i = threadIdx.x; i < k; i += blockDim.x) sx[i] -= A[(long long)k * n + i] * xk;
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[e * n + i] = (double)sx[i];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -305,7 +307,7 @@ struct Solver {
   double* hdev = nullptr;   // [2][MAXK]
   double* hhost = nullptr;  // pinned [2][MAXK]
   double* probe = nullptr;  // [n]
-  float* blocks = nullptr;  // [E][5Np][5Np]
+  float* blocks = nullptr;  // [E][5Np][5Np]: assembled blocks, then (in place) their inverses
   int* piv = nullptr;
   int* info = nullptr;
   bool bj_ready = false;
@@ -455,9 +457,9 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
   rc = bj_assemble(m, S, U, t, c, S->blocks, s, f32);
   if (rc) return rc;
   prof_begin(m, s, KK_LU);
-  k_lu<<<(unsigned)m->E, 256, 0, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+  k_gj_inverse<<<(unsigned)m->E, 256, sizeof(float) * 2 * nb, s>>>(m->E, nb, S->blocks, S->piv, S->info);
   prof_end(m, s);
-  DG_LAUNCH_CHECK("k_lu");
+  DG_LAUNCH_CHECK("k_gj_inverse");
   int info = 0;
   DG_CUDA_TRY(cudaMemcpyAsync(&info, S->info, sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -475,12 +477,25 @@ static int precond_apply(dg_mesh* m, Solver* S, int kind, const double* x, doubl
     if (!S->bj_ready) return fail(DG_EINVAL, "block-Jacobi preconditioner used before dg_precond_setup");
     const int nb = 5 * m->np;
     prof_begin(m, s, KK_PRECOND);
-    k_lu_solve<<<(unsigned)m->E, 128, sizeof(float) * nb, s>>>(m->E, nb, S->blocks, S->piv, x, y);
+    k_inv_apply<<<(unsigned)m->E, nb <= 128 ? 128 : 256, sizeof(float) * nb, s>>>(m->E, nb, S->blocks, x, y);
     prof_end(m, s);
-    DG_LAUNCH_CHECK("k_lu_solve");
+    DG_LAUNCH_CHECK("k_inv_apply");
     return DG_OK;
   }
+  if (kind == DG_PC_MLP) {
+    prof_begin(m, s, KK_PRECOND);
+    const int rc = mlp_apply(m, x, y, s);
+    prof_end(m, s);
+    return rc;
+  }
   return fail(DG_EINVAL, "unknown preconditioner kind");
+}
+
+// (re)build the preconditioner of kind at state U
+static int pc_setup(dg_mesh* m, Solver* S, int kind, const double* U, double t, double c, cudaStream_t s, bool f32) {
+  if (kind == DG_PC_BJ) return bj_setup(m, S, U, t, c, s, f32);
+  if (kind == DG_PC_MLP) return mlp_setup(m, U, c, s);
+  return DG_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -610,6 +625,7 @@ extern "C" int dg_precond_setup(dg_mesh* mesh, int32_t kind, const double* u, do
   if (rc) return rc;
   if (kind == DG_PC_NONE) return DG_OK;
   if (kind == DG_PC_BJ) return bj_setup(mesh, S, u, t, dt_aii, (cudaStream_t)stream);
+  if (kind == DG_PC_MLP) return mlp_setup(mesh, u, dt_aii, (cudaStream_t)stream);
   return fail(DG_EINVAL, "dg_precond_setup: unknown kind");
 }
 
@@ -651,9 +667,9 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
     if (stats) *stats = st;
     return code;
   };
-  if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_STEP) {
+  if (o.precond != DG_PC_NONE && o.precond_refresh == DG_REFRESH_STEP) {
     const auto p0 = std::chrono::steady_clock::now();
-    rc = bj_setup(mesh, S, un, t + c[0] * dt, dt * A[0][0], s, o.jv_prec == DG_PREC_F32);
+    rc = pc_setup(mesh, S, o.precond, un, t + c[0] * dt, dt * A[0][0], s, o.jv_prec == DG_PREC_F32);
     st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
     if (rc) return finish(rc);
   }
@@ -665,9 +681,9 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
     k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, Mun, i > 0 ? dt * A[i][0] : 0.0, i > 0 ? R[0] : nullptr,
                                           i > 1 ? dt * A[i][1] : 0.0, i > 1 ? R[1] : nullptr, known);
     DG_LAUNCH_CHECK("k_lincomb");
-    if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_STAGE) {
+    if (o.precond != DG_PC_NONE && o.precond_refresh == DG_REFRESH_STAGE) {
       const auto p0 = std::chrono::steady_clock::now();
-      rc = bj_setup(mesh, S, U, ti, ci, s, o.jv_prec == DG_PREC_F32);
+      rc = pc_setup(mesh, S, o.precond, U, ti, ci, s, o.jv_prec == DG_PREC_F32);
       st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
       if (rc) return finish(rc);
     }
@@ -695,9 +711,9 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
         break;
       }
       if (it == o.max_newton) break;
-      if (o.precond == DG_PC_BJ && o.precond_refresh == DG_REFRESH_NEWTON) {
+      if (o.precond != DG_PC_NONE && o.precond_refresh == DG_REFRESH_NEWTON) {
         const auto p0 = std::chrono::steady_clock::now();
-        rc = bj_setup(mesh, S, U, ti, ci, s, o.jv_prec == DG_PREC_F32);
+        rc = pc_setup(mesh, S, o.precond, U, ti, ci, s, o.jv_prec == DG_PREC_F32);
         st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
         if (rc) return finish(rc);
       }

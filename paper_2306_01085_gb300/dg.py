@@ -92,6 +92,13 @@ def lib():
     L.dg_probe_fp64.argtypes = [ctypes.POINTER(ctypes.c_double)]
     L.dg_residual_f32.argtypes = [vp, dp, d, dp, vp]
     L.dg_jvp_f32.argtypes = [vp, dp, dp, d, dp, dp, vp]
+    L.dg_mlp_init.argtypes = [vp, i32, i32, ctypes.c_int64, ctypes.c_uint64]
+    L.dg_mlp_sizes.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), i64p]
+    L.dg_mlp_params.argtypes = [vp, dp, dp, vp]
+    L.dg_mlp_features.argtypes = [vp, dp, d, dp, dp, vp]
+    L.dg_mlp_harvest.argtypes = [vp, dp, d, d, i32, i64p, vp]
+    L.dg_mlp_loss_grad.argtypes = [vp, dp, dp, i32, ctypes.POINTER(ctypes.c_double), dp, vp]
+    L.dg_mlp_train.argtypes = [vp, i32, i32, d, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     L.dg_solver_opts_default.argtypes = [ctypes.POINTER(DgSolverOpts)]
     L.dg_solver_opts_default.restype = None
     L.dg_dirk_tableau.argtypes = [i32, dp, dp]
@@ -322,3 +329,71 @@ def _mesh_jvp_f32(self, u, v, t=0.0, out=None, r_out=None):
 
 Mesh.residual_f32 = _mesh_residual_f32
 Mesh.jvp_f32 = _mesh_jvp_f32
+
+
+# -- learned preconditioner -------------------------------------------------------------------
+def _fptr(t, name):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise DgError(f"{name} must be a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _mesh_mlp_init(self, hidden=256, rank=16, max_samples=0, seed=7):
+    _check(lib().dg_mlp_init(self._h, hidden, rank, int(max_samples), int(seed)))
+
+
+def _mesh_mlp_sizes(self):
+    npar, nin, nout, ns = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().dg_mlp_sizes(self._h, ctypes.byref(npar), ctypes.byref(nin), ctypes.byref(nout), ctypes.byref(ns)))
+    return {"n_params": npar.value, "n_in": nin.value, "n_out": nout.value, "n_samples": ns.value}
+
+
+def _mesh_mlp_params(self, new=None):
+    import torch
+    out = torch.empty(self.mlp_sizes()["n_params"], dtype=torch.float32, device="cuda")
+    _check(lib().dg_mlp_params(self._h, _fptr(out, "out"), _fptr(new, "in"), _stream()))
+    return out
+
+
+def _mesh_mlp_features(self, u, dt_aii):
+    import torch
+    sz = self.mlp_sizes()
+    feat = torch.empty((self.n_elem, sz["n_in"]), dtype=torch.float32, device="cuda")
+    sd = torch.empty((self.n_elem, self.n_p), dtype=torch.float32, device="cuda")
+    _check(lib().dg_mlp_features(self._h, _ptr(u, self.u_shape, "u"), float(dt_aii), _fptr(feat, "feat"),
+                                 _fptr(sd, "sdiag"), _stream()))
+    return feat, sd
+
+
+def _mesh_mlp_harvest(self, u, t, dt_aii, stride=1):
+    n = ctypes.c_int64()
+    _check(lib().dg_mlp_harvest(self._h, _ptr(u, self.u_shape, "u"), float(t), float(dt_aii), int(stride),
+                                ctypes.byref(n), _stream()))
+    return n.value
+
+
+def _mesh_mlp_loss_grad(self, X, Bs):
+    import torch
+    g = torch.empty(self.mlp_sizes()["n_params"], dtype=torch.float32, device="cuda")
+    L = ctypes.c_double()
+    _check(lib().dg_mlp_loss_grad(self._h, _fptr(X, "X"), _fptr(Bs, "Bs"), int(X.shape[0]), ctypes.byref(L),
+                                  _fptr(g, "grad"), _stream()))
+    return L.value, g
+
+
+def _mesh_mlp_train(self, epochs, batch=512, lr=1e-3):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().dg_mlp_train(self._h, int(epochs), int(batch), float(lr), ctypes.byref(a), ctypes.byref(b), _stream()))
+    return a.value, b.value
+
+
+Mesh.mlp_init = _mesh_mlp_init
+Mesh.mlp_sizes = _mesh_mlp_sizes
+Mesh.mlp_params = _mesh_mlp_params
+Mesh.mlp_features = _mesh_mlp_features
+Mesh.mlp_harvest = _mesh_mlp_harvest
+Mesh.mlp_loss_grad = _mesh_mlp_loss_grad
+Mesh.mlp_train = _mesh_mlp_train
