@@ -123,6 +123,9 @@ namespace dg {
 int ensure_f32(dg_mesh* m);       // allocate and fill the FP32 workspace and geometry
 }
 int mlp_setup(dg_mesh* mesh, const double* u, double dt_aii, cudaStream_t s);
+// J_G v = M v - c J_r(u) v in one tangent pass (exact tangent; FP32 arithmetic when f32)
+int stage_jvp(dg_mesh* mesh, const double* u, const double* v, double t, double c, double* out, bool f32,
+              cudaStream_t s);
 int mlp_apply(dg_mesh* mesh, const double* x, double* y, cudaStream_t s);
 
 void dg_solver_release(dg_mesh* m);
@@ -155,7 +158,7 @@ struct Driver {
   // f32: FP32 data and arithmetic (exp(log rho) in FP64); inputs and outputs stay FP64
   static int gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32 = false);
   static int residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
-                      bool tangent, cudaStream_t s, bool f32 = false);
+                      bool tangent, cudaStream_t s, bool f32 = false, double stage_c = 0.0);
   static int q_to_nodal(dg_mesh* m, double* q, cudaStream_t s);
   static int q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s);
   static int mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
@@ -163,7 +166,8 @@ struct Driver {
   static int jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s,
                           bool f32 = false);
   template <typename R> static int gradient_p(dg_mesh* m, const double* u, const double* v, cudaStream_t s);
-  template <typename R> static int residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s);
+  template <typename R>
+  static int residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s, double stage_c);
   template <typename R>
   static int jv_blockdiag_p(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s);
 };

@@ -501,12 +501,14 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
   for (int c = 0; c < 5; ++c) src[c] = src[c] * Wd;
 }
 
+// stage_c != 0 (NC = 2): the tangent output is the DIRK stage operator J_G v = M v - stage_c J_r v,
+// M v = B^T (W B v) being formed from the tangent's own Gauss values
 template <int N, int NC, typename R>
 __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
                          const R* __restrict__ geo, const R* __restrict__ accg,
                          const R* __restrict__ xg, const R* __restrict__ ug,
                          const R* __restrict__ qg, const R* __restrict__ fh,
-                         double* __restrict__ r, double* __restrict__ jv) {
+                         double* __restrict__ r, double* __restrict__ jv, R stage_c) {
   using S = typename std::conditional<NC == 2, DualT<R>, R>::type;
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
   __shared__ SmemOpsT<R> so;
@@ -532,6 +534,7 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R
   const long long e = e0 + el;
   const bool active = el < EPB && e < E;
   S srcv[5];
+  R wu[5] = {R(0), R(0), R(0), R(0), R(0)};   // W u_dot at this point (stage operator)
   if (active) {
     const long long plane_g = E * 5 * NP, plane_q = E * 15 * NP;
     S u[5], q[3][5];
@@ -555,6 +558,10 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R
     }
     S Fref[3][5];
     volume_point<S>(P, u, q, G, Wd, a3, x3, t, Fref, srcv);
+    if constexpr (NC == 2) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) wu[c] = Wd * u[c].d;
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -581,6 +588,7 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R
         const R coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
         acc = fma(-coef, sH[((el * 6 + phi) * C + c) * NF + vol_face_point<N>(g, axis)], acc);
       }
+      if (NC == 2 && c >= 5 && stage_c != R(0)) acc = wu[c - 5] - stage_c * acc;
       sR[(el * C + c) * NP + g] = acc;
     }
   }
@@ -609,27 +617,32 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R
 // --------------------------------------------------------------------------------------------
 // tensor transforms of nodal q and the mass matrix
 // --------------------------------------------------------------------------------------------
-// out = A x A x A in (T: A^T) for C components per element, then optionally face traces of out
+// out = A x A x A in (T: A^T) for C components of EPB elements per CTA (one thread per point of
+// each element), optional W-weighting and back-transform (mass matrix), optional face traces
 template <int N, bool T, int C>
 __global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, const double* __restrict__ in_g,
                          double* __restrict__ out_g, const double* __restrict__ weight,
                          double* __restrict__ traces) {
-  constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF;
+  constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, EPB = Epb<N, 1>::value;
   __shared__ SmemOps so;
   extern __shared__ double smem[];
-  double* b0 = smem;
-  double* b1 = smem + C * NP;
+  double* b0 = smem;                 // [EPB][C][NP]
+  double* b1 = smem + EPB * C * NP;  // [EPB][C][NP]
   load_ops<N, double>(ops, so);
-  const long long e = blockIdx.x;
-  const int g = threadIdx.x;
-  for (int idx = threadIdx.x; idx < C * NP; idx += blockDim.x) b0[idx] = in_g[e * C * NP + idx];
+  const long long e0 = (long long)blockIdx.x * EPB;
+  for (int idx = threadIdx.x; idx < EPB * C * NP; idx += blockDim.x) {
+    const long long e = e0 + idx / (C * NP);
+    if (e < E) b0[idx] = in_g[e0 * C * NP + idx];
+  }
   __syncthreads();
+  const int el = threadIdx.x / NP, g = threadIdx.x % NP;
+  const bool active = el < EPB && (e0 + el) < E;
   const double* A = (which == 0) ? so.B : so.Binv;
   double* in = b0;
   double* out = b1;
   for (int dir = 0; dir < 3; ++dir) {
-    if (g < NP)
-      for (int c = 0; c < C; ++c) out[c * NP + g] = line<N, T>(A, in + c * NP, g, dir);
+    if (active)
+      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, T>(A, in + (el * C + c) * NP, g, dir);
     __syncthreads();
     double* tt = in;
     in = out;
@@ -637,28 +650,34 @@ __global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, co
   }
   if (weight) {
     // mass matrix: W-weighted Gauss values, then back with B^T
-    if (g < NP) {
-      const double wd = weight[e * 10 * NP + 9 * NP + g];
-      for (int c = 0; c < C; ++c) in[c * NP + g] *= wd;
+    if (active) {
+      const double wd = weight[(e0 + el) * 10 * NP + 9 * NP + g];
+      for (int c = 0; c < C; ++c) in[(el * C + c) * NP + g] *= wd;
     }
     __syncthreads();
     for (int dir = 0; dir < 3; ++dir) {
-      if (g < NP)
-        for (int c = 0; c < C; ++c) out[c * NP + g] = line<N, true>(A, in + c * NP, g, dir);
+      if (active)
+        for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, true>(A, in + (el * C + c) * NP, g, dir);
       __syncthreads();
       double* tt = in;
       in = out;
       out = tt;
     }
   }
-  for (int idx = threadIdx.x; idx < C * NP; idx += blockDim.x) out_g[e * C * NP + idx] = in[idx];
+  for (int idx = threadIdx.x; idx < EPB * C * NP; idx += blockDim.x) {
+    const long long e = e0 + idx / (C * NP);
+    if (e < E) out_g[e0 * C * NP + idx] = in[idx];
+  }
   if (traces) {
-    for (int idx = threadIdx.x; idx < 6 * C * NF; idx += blockDim.x) {
-      const int phi = idx / (C * NF), c = (idx / NF) % C, f = idx % NF;
+    for (int idx = threadIdx.x; idx < EPB * 6 * C * NF; idx += blockDim.x) {
+      const int l = idx / (6 * C * NF), rem = idx % (6 * C * NF);
+      const long long e = e0 + l;
+      if (e >= E) continue;
+      const int phi = rem / (C * NF), c = (rem / NF) % C, f = rem % NF;
       const double* ev = (phi & 1) ? so.eR : so.eL;
       double acc = 0.0;
-      for (int k = 0; k < N; ++k) acc = fma(ev[k], in[c * NP + face_vol_point<N>(phi, f, k)], acc);
-      traces[e * 6 * C * NF + idx] = acc;
+      for (int k = 0; k < N; ++k) acc = fma(ev[k], in[(l * C + c) * NP + face_vol_point<N>(phi, f, k)], acc);
+      traces[e * 6 * C * NF + rem] = acc;
     }
   }
 }
@@ -845,7 +864,7 @@ static int run_faces(dg_mesh* m, cudaStream_t s) {
 }
 
 template <int N, int NC, typename R = double>
-static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t s) {
+static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t s, double stage_c = 0.0) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
   const size_t sm = Smem<N, NC, R>::volume;
   int rc = set_smem(k_volume<N, NC, R>, sm);
@@ -854,7 +873,7 @@ static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t 
   const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_VOLUME);
   k_volume<N, NC, R><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), (R)t, w.geo, w.acc, w.xg,
-                                                   w.ug, w.qg, w.fh, r, jv);
+                                                   w.ug, w.qg, w.fh, r, jv, (R)stage_c);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_volume");
   return DG_OK;
@@ -886,10 +905,11 @@ int Driver<N>::gradient_p(dg_mesh* m, const double* u, const double* v, cudaStre
 
 template <int N>
 template <typename R>
-int Driver<N>::residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s) {
+int Driver<N>::residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s,
+                          double stage_c) {
   int rc = tangent ? run_faces<N, 2, false, R>(m, s) : run_faces<N, 1, false, R>(m, s);
   if (rc) return rc;
-  return tangent ? run_volume<N, 2, R>(m, t, r, jv, s) : run_volume<N, 1, R>(m, t, r, nullptr, s);
+  return tangent ? run_volume<N, 2, R>(m, t, r, jv, s, stage_c) : run_volume<N, 1, R>(m, t, r, nullptr, s);
 }
 
 template <int N>
@@ -899,10 +919,11 @@ int Driver<N>::gradient(dg_mesh* m, const double* u, const double* v, cudaStream
 
 template <int N>
 int Driver<N>::residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
-                        bool tangent, cudaStream_t s, bool f32) {
+                        bool tangent, cudaStream_t s, bool f32, double stage_c) {
   (void)u;
   (void)v;
-  return f32 ? residual_p<float>(m, t, r, jv, tangent, s) : residual_p<double>(m, t, r, jv, tangent, s);
+  return f32 ? residual_p<float>(m, t, r, jv, tangent, s, stage_c)
+             : residual_p<double>(m, t, r, jv, tangent, s, stage_c);
 }
 
 template <int N>
@@ -927,12 +948,13 @@ int Driver<N>::jv_blockdiag(dg_mesh* m, const double* u, const double* probe, do
 template <int N>
 int Driver<N>::q_to_nodal(dg_mesh* m, double* q, cudaStream_t s) {
   constexpr int NP = Shape<N>::NP;
-  const size_t sm = sizeof(double) * 2 * 15 * NP;
+  constexpr int EPB = Epb<N, 1>::value;
+  const size_t sm = sizeof(double) * 2 * EPB * 15 * NP;
   int rc = set_smem(k_tensor<N, false, 15>, sm);
   if (rc) return rc;
   prof_begin(m, s, KK_TENSOR);
-  k_tensor<N, false, 15><<<(unsigned)m->E, NP < 32 ? 32 : NP, sm, s>>>(m->E, m->d_ops, 1, m->ws.qg, q, nullptr,
-                                                                      nullptr);
+  k_tensor<N, false, 15><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, 1, m->ws.qg, q,
+                                                                                   nullptr, nullptr);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_tensor(q nodal)");
   return DG_OK;
@@ -941,12 +963,13 @@ int Driver<N>::q_to_nodal(dg_mesh* m, double* q, cudaStream_t s) {
 template <int N>
 int Driver<N>::q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) {
   constexpr int NP = Shape<N>::NP;
-  const size_t sm = sizeof(double) * 2 * 15 * NP;
+  constexpr int EPB = Epb<N, 1>::value;
+  const size_t sm = sizeof(double) * 2 * EPB * 15 * NP;
   int rc = set_smem(k_tensor<N, false, 15>, sm);
   if (rc) return rc;
   prof_begin(m, s, KK_TENSOR);
-  k_tensor<N, false, 15><<<(unsigned)m->E, NP < 32 ? 32 : NP, sm, s>>>(m->E, m->d_ops, 0, q, m->ws.qg, nullptr,
-                                                                      m->ws.qf);
+  k_tensor<N, false, 15><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, 0, q, m->ws.qg,
+                                                                                   nullptr, m->ws.qf);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_tensor(q gauss)");
   return DG_OK;
@@ -955,11 +978,13 @@ int Driver<N>::q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) {
 template <int N>
 int Driver<N>::mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s) {
   constexpr int NP = Shape<N>::NP;
-  const size_t sm = sizeof(double) * 2 * 5 * NP;
+  constexpr int EPB = Epb<N, 1>::value;
+  const size_t sm = sizeof(double) * 2 * EPB * 5 * NP;
   int rc = set_smem(k_tensor<N, false, 5>, sm);
   if (rc) return rc;
   prof_begin(m, s, KK_TENSOR);
-  k_tensor<N, false, 5><<<(unsigned)m->E, NP < 32 ? 32 : NP, sm, s>>>(m->E, m->d_ops, 0, v, mv, m->geo, nullptr);
+  k_tensor<N, false, 5><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, 0, v, mv, m->geo,
+                                                                                  nullptr);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_tensor(mass)");
   return DG_OK;

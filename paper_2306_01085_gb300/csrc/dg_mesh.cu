@@ -34,8 +34,8 @@ static int drv_gradient(dg_mesh* m, const double* u, const double* v, cudaStream
   DG_DISPATCH(m, gradient(m, u, v, s, f32));
 }
 static int drv_residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
-                        bool tan, cudaStream_t s, bool f32 = false) {
-  DG_DISPATCH(m, residual(m, u, v, t, r, jv, tan, s, f32));
+                        bool tan, cudaStream_t s, bool f32 = false, double stage_c = 0.0) {
+  DG_DISPATCH(m, residual(m, u, v, t, r, jv, tan, s, f32, stage_c));
 }
 static int drv_q_to_nodal(dg_mesh* m, double* q, cudaStream_t s) { DG_DISPATCH(m, q_to_nodal(m, q, s)); }
 static int drv_q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) { DG_DISPATCH(m, q_from_nodal(m, q, s)); }
@@ -675,4 +675,16 @@ extern "C" int dg_jvp_f32(dg_mesh* mesh, const double* u, const double* v, doubl
   rc = drv_gradient(mesh, u, v, s, true);
   if (rc) return rc;
   return drv_residual(mesh, u, v, t, r_out, jv, true, s, true);
+}
+
+int stage_jvp(dg_mesh* mesh, const double* u, const double* v, double t, double c, double* out, bool f32,
+              cudaStream_t s) {
+  if (c == 0.0) return fail(DG_EINVAL, "stage operator needs dt a_ii != 0");
+  if (f32) {
+    int rc = ensure_f32(mesh);
+    if (rc) return rc;
+  }
+  int rc = drv_gradient(mesh, u, v, s, f32);
+  if (rc) return rc;
+  return drv_residual(mesh, u, v, t, nullptr, out, true, s, f32, c);
 }

@@ -126,28 +126,39 @@ __global__ void k_scale_dev(long long n, const double* __restrict__ x, const dou
     out[i] = x[i] * s;
 }
 
-// partial[j][block] = sum_i V_j[i] w[i] for j < k; partial[k][block] = sum_i w[i]^2
-__global__ void k_mdot(long long n, int k, const double* __restrict__ V, long long ldv,
-                       const double* __restrict__ w, double* __restrict__ partial) {
-  __shared__ double red[RED_THREADS];
-  double acc[MAXK];
-#pragma unroll 1
-  for (int j = 0; j <= k; ++j) acc[j] = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double wi = w[i];
-#pragma unroll 1
-    for (int j = 0; j < k; ++j) acc[j] = fma(V[j * ldv + i], wi, acc[j]);
-    acc[k] = fma(wi, wi, acc[k]);
-  }
-#pragma unroll 1
-  for (int j = 0; j <= k; ++j) {
-    red[threadIdx.x] = acc[j];
-    __syncthreads();
-    for (int st = RED_THREADS / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-      __syncthreads();
+// partial[j][block] = sum_i V_j[i] w[i] for j < k; partial[k][block] = sum_i w[i]^2.
+// Vectors are taken 16 at a time (one pass over w per group) so the accumulators stay in
+// registers; warp-shuffle and cross-warp reductions, fixed order.
+constexpr int MDOT_G = 16;
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(long long n, int k, const double* __restrict__ V, long long ldv,
+                                                     const double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double red[RED_THREADS / 32][MDOT_G];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j0 = 0; j0 <= k; j0 += MDOT_G) {
+    double acc[MDOT_G];
+#pragma unroll
+    for (int j = 0; j < MDOT_G; ++j) acc[j] = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int j = 0; j < MDOT_G; ++j) {
+        const int jj = j0 + j;
+        if (jj < k) acc[j] = fma(V[jj * ldv + i], wi, acc[j]);
+        else if (jj == k) acc[j] = fma(wi, wi, acc[j]);
+      }
     }
-    if (threadIdx.x == 0) partial[j * RED_BLOCKS + blockIdx.x] = red[0];
+#pragma unroll
+    for (int j = 0; j < MDOT_G; ++j) {
+      double v = acc[j];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < MDOT_G && j0 + threadIdx.x <= k) {
+      double v = 0.0;
+      for (int q = 0; q < RED_THREADS / 32; ++q) v += red[q][threadIdx.x];
+      partial[(j0 + threadIdx.x) * RED_BLOCKS + blockIdx.x] = v;
+    }
     __syncthreads();
   }
 }
@@ -210,13 +221,19 @@ __global__ void k_scatter_col(long long E, int n, int j, double c, const double*
 // k, scale row k by the reciprocal pivot (the pivot position takes the reciprocal itself) and
 // eliminate column k from every other row (that column takes -a_ik / pivot). After n steps the
 // columns are interchanged back in reverse pivot order, leaving A^{-1}.
+template <bool SMEM>
 __global__ void k_gj_inverse(long long E, int n, float* __restrict__ blocks, int* __restrict__ piv,
                              int* __restrict__ info) {
   extern __shared__ float sfr[];
   float* f = sfr;        // column k before the step
   float* r = sfr + n;    // scaled row k
   const long long e = blockIdx.x;
-  float* A = blocks + e * (long long)n * n;
+  float* Ag = blocks + e * (long long)n * n;
+  float* A = SMEM ? sfr + 2 * n : Ag;   // the block itself, in shared memory when it fits
+  if (SMEM) {
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = Ag[t];
+    __syncthreads();
+  }
   int* pv = piv + e * n;
   __shared__ float sval[256];
   __shared__ int sidx[256];
@@ -261,10 +278,18 @@ __global__ void k_gj_inverse(long long E, int n, float* __restrict__ blocks, int
     for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = A[(long long)k * n + i];
     for (int j = threadIdx.x; j < n; j += blockDim.x) r[j] = (j == k ? 1.0f : A[(long long)j * n + k]) * pinv;
     __syncthreads();
-    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
-      const int j = (int)(t / n), i = (int)(t % n);
-      if (i == k) A[t] = r[j];
-      else A[t] = (j == k ? 0.0f : A[t]) - f[i] * r[j];
+    // rank-1 elimination: columns by warp, rows by lane (coalesced, no index division)
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int j = warp; j < n; j += nw) {
+        float* col = A + (long long)j * n;
+        const float rj = r[j];
+        if (j == k) {
+          for (int i = lane; i < n; i += 32) col[i] = (i == k) ? rj : -f[i] * rj;
+        } else {
+          for (int i = lane; i < n; i += 32) col[i] = (i == k) ? rj : fmaf(-f[i], rj, col[i]);
+        }
+      }
     }
     __syncthreads();
   }
@@ -278,6 +303,8 @@ __global__ void k_gj_inverse(long long E, int n, float* __restrict__ blocks, int
       }
     __syncthreads();
   }
+  if (SMEM)
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ag[t] = A[t];
 }
 
 // y = B^{-1} x per element with the explicit FP32 inverse (column-major): coalesced over rows
@@ -289,9 +316,18 @@ __global__ void k_inv_apply(long long E, int n, const float* __restrict__ inv, c
   for (int i = threadIdx.x; i < n; i += blockDim.x) sx[i] = (float)x[e * n + i];
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float acc = 0.f;
-    for (int j = 0; j < n; ++j) acc = fmaf(A[(long long)j * n + i], sx[j], acc);
-    y[e * n + i] = (double)acc;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    const float* a = A + i;
+    int j = 0;
+#pragma unroll 2
+    for (; j + 3 < n; j += 4) {
+      acc0 = fmaf(a[(long long)j * n], sx[j], acc0);
+      acc1 = fmaf(a[(long long)(j + 1) * n], sx[j + 1], acc1);
+      acc2 = fmaf(a[(long long)(j + 2) * n], sx[j + 2], acc2);
+      acc3 = fmaf(a[(long long)(j + 3) * n], sx[j + 3], acc3);
+    }
+    for (; j < n; ++j) acc0 = fmaf(a[(long long)j * n], sx[j], acc0);
+    y[e * n + i] = (double)((acc0 + acc1) + (acc2 + acc3));
   }
 }
 
@@ -389,13 +425,12 @@ static unsigned grid_for(long long n) {
 // J_G v = M v - c J_r(U) v
 static int stage_matvec(dg_mesh* m, Solver* S, const double* U, double t, double c, int jv_mode, int jv_prec,
                         const double* v, double* out, cudaStream_t s) {
+  // exact tangent: one fused pass forms M v - c J_r v
+  if (jv_mode == DG_JV_EXACT) return stage_jvp(m, U, v, t, c, out, jv_prec == DG_PREC_F32, s);
   double* mv = S->v(VTMP);
   int rc = dg_mass_apply(m, v, mv, s);
   if (rc) return rc;
-  if (jv_prec == DG_PREC_F32 && jv_mode == DG_JV_EXACT)
-    rc = dg_jvp_f32(m, U, v, t, out, nullptr, s);
-  else
-    rc = dg_jvp(m, U, v, t, jv_mode, 0.0, out, nullptr, s);
+  rc = dg_jvp(m, U, v, t, jv_mode, 0.0, out, nullptr, s);
   if (rc) return rc;
   prof_begin(m, s, KK_BLAS);
   k_lincomb<<<grid_for(S->n), 256, 0, s>>>(S->n, 1.0, mv, -c, out, 0.0, nullptr, out);
@@ -457,7 +492,13 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
   rc = bj_assemble(m, S, U, t, c, S->blocks, s, f32);
   if (rc) return rc;
   prof_begin(m, s, KK_LU);
-  k_gj_inverse<<<(unsigned)m->E, 256, sizeof(float) * 2 * nb, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+  const size_t gj_smem = sizeof(float) * (2 * nb + (size_t)nb * nb);
+  if (gj_smem <= 200 * 1024) {
+    cudaFuncSetAttribute(k_gj_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem);
+    k_gj_inverse<true><<<(unsigned)m->E, 256, gj_smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+  } else {
+    k_gj_inverse<false><<<(unsigned)m->E, 256, sizeof(float) * 2 * nb, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+  }
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_gj_inverse");
   int info = 0;
@@ -477,7 +518,7 @@ static int precond_apply(dg_mesh* m, Solver* S, int kind, const double* x, doubl
     if (!S->bj_ready) return fail(DG_EINVAL, "block-Jacobi preconditioner used before dg_precond_setup");
     const int nb = 5 * m->np;
     prof_begin(m, s, KK_PRECOND);
-    k_inv_apply<<<(unsigned)m->E, nb <= 128 ? 128 : 256, sizeof(float) * nb, s>>>(m->E, nb, S->blocks, x, y);
+    k_inv_apply<<<(unsigned)m->E, nb <= 256 ? (nb + 31) / 32 * 32 : 256, sizeof(float) * nb, s>>>(m->E, nb, S->blocks, x, y);
     prof_end(m, s);
     DG_LAUNCH_CHECK("k_inv_apply");
     return DG_OK;
