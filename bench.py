@@ -32,6 +32,17 @@ CONFIG_NAME = "shell16x8_p4"
 L2_BYTES = 129 * 2 ** 20
 
 
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -46,6 +57,8 @@ def parse():
                     help="time the implicit DIRK step variants instead (configs shell32x16_p2_euv, shell48x16_p3_euv)")
     ap.add_argument("--variants", default="plain_bj,mixed_bj,mixed_mlp,plain_none",
                     help="comma list for --implicit: plain_bj, mixed_bj, plain_none, mixed_mlp")
+    ap.add_argument("--precision", action="store_true",
+                    help="contraction precision study (FP32 / bf16 / fp16 and split variants) instead")
     ap.add_argument("--mlp-steps", type=int, default=2, help="plain steps whose blocks train the network")
     ap.add_argument("--mlp-epochs", type=int, default=20)
     return ap.parse_args()
@@ -157,9 +170,41 @@ class ClockSampler:
 # (profiles/fp64_residual_jv_shell16x8_p4.md); only valid for the kernels of that capture, so the
 # table is keyed by the source digest of the library it was measured on.
 # ----------------------------------------------------------------------------------------------
-FP64_FLOPS_PER_ELEMENT = {("k_grad", 5): 247981.3, ("k_volume", 5): 205500.0, ("k_faces", 5): 84125.0}
-DRAM_BYTES_PER_LAUNCH = {("k_grad", 5): 1206637056.0, ("k_volume", 5): 912731136.0, ("k_faces", 5): 755406848.0}
-CAPTURE_DIGEST = "ba3430f89bcfb9b533d92c861ce8c397f31d3b7678f5f17fb0398a47cc7d1150"   # build digest of the library these counters were taken on
+def grad_flops_per_element(N, NC=2):
+    """FP64 flops of the sum-factorised LDG gradient (k_grad) per element, counted from the
+    algorithm (an FMA is 2 flops): per component c, at each of the N^3 Gauss points G u (9),
+    the lifting sum over 6 faces and 3 directions (36), the weak derivative D^T over 3 axes and 3
+    directions (18 N) and the 1/(w |J|) scaling (3); at each of the 6 N^2 face points the trace
+    average (2), (w n dS) u_hat (3) and the extrapolation of the 3 new gradient components (6 N)."""
+    NP, NF = N ** 3, N ** 2
+    return 5 * NC * (NP * (48 + 18 * N) + 6 * NF * (5 + 6 * N))
+
+
+# FP64 flops per element: k_grad from the algorithm; k_volume and k_faces (pointwise physics
+# dominated) as executed, (2 DFMA + DMUL + DADD) thread instructions of the ncu capture of the
+# residual kernels whose source digest is CAPTURE_DIGEST (profiles/fp64_residual_jv_shell16x8_p4.md)
+FP64_FLOPS_PER_ELEMENT = {("k_grad", 5): float(grad_flops_per_element(5)), ("k_volume", 5): 210941.9,
+                          ("k_faces", 5): 84234.6}
+FLOPS_KIND = {"k_grad": "algorithmic (sum-factorisation count)", "k_volume": "executed (ncu instruction counts)",
+              "k_faces": "executed (ncu instruction counts)"}
+DRAM_BYTES_PER_LAUNCH = {("k_grad", 5): 1206033408.0, ("k_volume", 5): 912070912.0, ("k_faces", 5): 755091456.0}
+CAPTURE_DIGEST = "595cdc2a78c22aba8dd126c87b8314331b294a587060e2016dffc5eb7fdb561c"
+RESIDUAL_SOURCES = ("dg_kernels.cuh", "dg_internal.cuh", "dg_map.cuh", "dg_kernels_n5.cu")
+
+
+def residual_kernel_digest():
+    """sha256 of the sources of the p = 4 residual kernels and the compile flags."""
+    import hashlib
+    from paper_2306_01085_gb300 import build as B
+    h = hashlib.sha256()
+    for f in RESIDUAL_SOURCES:
+        with open(os.path.join(B.CSRC, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    h.update(" ".join(B.ARCH + B.FLAGS).encode())
+    return h.hexdigest()
+
+
 # FP64 peak from unit counts: 2 DFMA lanes/SM/cycle x 152 SMs x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
@@ -239,15 +284,21 @@ def main_ours(args):
     flops = FP64_FLOPS_PER_ELEMENT.get(key, float("nan")) * mesh.n_elem
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     probe = DG.probe_fp64()
-    fresh = B._digest() == CAPTURE_DIGEST
+    fresh = residual_kernel_digest() == CAPTURE_DIGEST
     traffic = DRAM_BYTES_PER_LAUNCH.get(key) if (args.config == CONFIG_NAME and fresh) else None
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "peak_kind": "FP64 from unit counts x max SM clock (2 DFMA/SM/cycle, 152 SMs, 2.07 GHz)",
+                "flops_kind": FLOPS_KIND.get(dom_name),
                 "peak_probe": round(probe, 4), "launch_ms": round(per_launch_ms, 4), "fp64_flops_per_launch": flops,
                 "share": round(dom_ms / sum(v[0] for v in prof.values()), 4),
-                "counters": "ncu capture of this build" if fresh else "ncu capture of an earlier build (flops as then)",
+                "counters": "ncu capture of these kernel sources" if fresh else "ncu capture of earlier kernel sources (flops as then)",
                 "dram_gbs": round(traffic / (per_launch_ms * 1e-3) / 1e9, 1) if traffic else None}
+
+    # the whole step against HBM: the two-pass minimum of 144 B/DOF (u, v in; q, q_dot out; u, q,
+    # v, q_dot in; r, Jv out)
+    roofline["hbm_context"] = {"bytes_per_dof": 144, "achieved_gbs": round(144 * mesh.n_dof / (ms_max * 1e-3) / 1e9, 1),
+                               "peak_gbs": HBM_PEAK_GBS, "frac": round(144 * mesh.n_dof / (ms_max * 1e-3) / 1e9 / HBM_PEAK_GBS, 4)}
 
     # end to end through the public API: pinned host in, host out, every step
     e2e = None
@@ -422,10 +473,73 @@ def main_implicit(args):
     mesh.close()
 
 
+def main_precision(args):
+    """Precision study of the basis contractions on one GPU: the fused residual + exact Jv with the
+    contractions in FP32, bfloat16 and binary16 operands (FP32 accumulation), and their hi + lo
+    three-product splits, each timed (2x L2 written between steps) and compared per variable with
+    the FP64 path on the same input (the FP64 path itself agrees with the oracle to 1e-12)."""
+    import numpy as np
+    import torch
+    from paper_2306_01085_gb300 import build as B
+    from paper_2306_01085_gb300 import dg as DG
+    from paper_2306_01085_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    config = args.config if args.config != CONFIG_NAME else "shell32x16_p2_euv"
+    desc = W.CONFIGS[config][0]()
+    mesh = DG.Mesh(desc)
+    u = W.state_for(desc, mesh.nodes().cpu().numpy(), 2)
+    v = W.unit_vector(102, u.shape)
+    ug = torch.from_numpy(u).cuda()
+    vg = torch.from_numpy(v).cuda()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    r64, j64 = mesh.empty(), mesh.empty()
+    mesh.jvp(ug, vg, t=0.0, out=j64, r_out=r64)
+    ref_r = np.moveaxis(r64.cpu().numpy(), 1, 0).reshape(5, -1)
+    ref_j = np.moveaxis(j64.cpu().numpy(), 1, 0).reshape(5, -1)
+    r, jv = mesh.empty(), mesh.empty()
+    modes = {"fp64": lambda: mesh.jvp(ug, vg, t=0.0, out=jv, r_out=r)}
+    for name in DG.CM:
+        modes[name] = (lambda nm: lambda: mesh.eval_precision(nm, ug, vg, t=0.0, r=r, jv=jv))(name)
+    out = {"metric": "fused residual + Jv DOFs/s and relative error per variable by contraction precision",
+           "config": config, "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "steps": args.steps,
+           "reference": "FP64 path on the same input", "modes": {}}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, fn in modes.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        gr = np.moveaxis(r.cpu().numpy(), 1, 0).reshape(5, -1)
+        gj = np.moveaxis(jv.cpu().numpy(), 1, 0).reshape(5, -1)
+        with np.errstate(invalid="ignore"):
+            er = (np.abs(gr - ref_r).max(1) / np.abs(ref_r).max(1)).tolist()
+            ej = (np.abs(gj - ref_j).max(1) / np.abs(ref_j).max(1)).tolist()
+        out["modes"][name] = {"ms": round(ms, 4), "dof_per_s": mesh.n_dof / (ms * 1e-3),
+                              "rel_err_r": [float(f"{x:.3e}") for x in er],
+                              "rel_err_jv": [float(f"{x:.3e}") for x in ej]}
+    out["clocks"] = clocks.stop()
+    print(json.dumps(out), flush=True)
+    mesh.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.implicit:
         main_implicit(a)
+        sys.exit(0)
+    if a.precision:
+        main_precision(a)
         sys.exit(0)
     if a.cpu_worker:
         cpu_worker(a.config, a.steps, a.cpu_worker)

@@ -142,6 +142,26 @@ int dg_jvp(dg_mesh* mesh, const double* u, const double* v, double t, int32_t mo
 int dg_residual_f32(dg_mesh* mesh, const double* u, double t, double* r, void* stream);
 int dg_jvp_f32(dg_mesh* mesh, const double* u, const double* v, double t, double* jv, double* r_out, void* stream);
 
+/*
+ * Precision study of the basis contractions (interpolation to Gauss points, face extrapolation,
+ * weak derivatives, lifting, projection back to the nodes) on top of the FP32 variant:
+ *   DG_CM_FP32   FP32 operands (same as dg_residual_f32 / dg_jvp_f32)
+ *   DG_CM_BF16   operands rounded to bfloat16, products exact, FP32 accumulation
+ *   DG_CM_FP16   operands rounded to binary16, products exact, FP32 accumulation
+ *   DG_CM_BF16X3 each operand split into bf16 hi + lo, three products (hi hi + hi lo + lo hi)
+ *   DG_CM_FP16X3 the same with binary16 parts
+ * The arithmetic of each contraction is that of a tensor-core MMA with FP32 accumulation; the
+ * pointwise fluxes stay FP32 and exp(varrho/2) FP64. Computes r (v == NULL) or the fused r and exact
+ * J v (r may then be NULL). FP64 inputs and outputs.
+ */
+#define DG_CM_FP32   0
+#define DG_CM_BF16   1
+#define DG_CM_FP16   2
+#define DG_CM_BF16X3 3
+#define DG_CM_FP16X3 4
+int dg_eval_precision(dg_mesh* mesh, int32_t mode, const double* u, const double* v, double t, double* r,
+                      double* jv, void* stream);
+
 /* Mass matrix product (M v)_i = sum_j (phi_i, phi_j) v_j per element and variable (Sec. 3.1). */
 int dg_mass_apply(dg_mesh* mesh, const double* v, double* mv, void* stream);
 

@@ -1,6 +1,6 @@
 """Learned element preconditioner: network, loss and gradients (oracle; test infrastructure only).
 
-The paper has no learned component; this is the benchmark spec's learned right preconditioner. Per
+The paper has no learned component; this is the library's learned right preconditioner. Per
 element, a multilayer perceptron with two hidden layers and SiLU activations maps element features
 x to o = W3 s(W2 s(W1 x + b1) + b2) + b3, s(z) = z / (1 + e^{-z}), read as
 

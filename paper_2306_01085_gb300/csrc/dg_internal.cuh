@@ -165,6 +165,11 @@ struct Driver {
   // J_r probe restricted to each element's own diagonal block (exact, one column per element)
   static int jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s,
                           bool f32 = false);
+  // FP32 residual (v == NULL) or fused residual + exact Jv with a contraction mode (CM_*)
+  static int eval_cm(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv, int cm,
+                     cudaStream_t s);
+  template <int CM>
+  static int eval_cm_t(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv, cudaStream_t s);
   template <typename R> static int gradient_p(dg_mesh* m, const double* u, const double* v, cudaStream_t s);
   template <typename R>
   static int residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s, double stage_c);

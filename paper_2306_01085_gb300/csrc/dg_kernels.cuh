@@ -24,6 +24,8 @@
 // The exact Jacobian-vector product carries forward-mode dual numbers through every step.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -50,15 +52,56 @@ __device__ __forceinline__ int pt_stride(int dir) {
   return dir == 0 ? 1 : (dir == 1 ? N : N * N);
 }
 
+// Contraction modes of the basis operators (the FP32 path only): CM_NATIVE multiplies in the
+// working precision; CM_BF16 / CM_FP16 round both operands to bfloat16 / binary16 and accumulate
+// in FP32 (the products of two such values are exact in FP32, as in a tensor-core MMA);
+// CM_BF16X3 / CM_FP16X3 split each operand into hi + lo parts and keep three of the four products
+// (hi*hi + hi*lo + lo*hi).
+enum { CM_NATIVE = 0, CM_BF16 = 1, CM_FP16 = 2, CM_BF16X3 = 3, CM_FP16X3 = 4 };
+
+template <int CM> __device__ __forceinline__ float cm_round(float v);
+template <> __device__ __forceinline__ float cm_round<CM_BF16>(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+template <> __device__ __forceinline__ float cm_round<CM_FP16>(float v) { return __half2float(__float2half_rn(v)); }
+
+template <int CM, typename R>
+__device__ __forceinline__ R cm_fma(R a, R x, R acc) {
+  if constexpr (CM == CM_NATIVE) {
+    return fma(a, x, acc);
+  } else {
+    constexpr int B = (CM == CM_BF16 || CM == CM_BF16X3) ? CM_BF16 : CM_FP16;
+    const float ah = cm_round<B>(a), xh = cm_round<B>(x);
+    if constexpr (CM == CM_BF16 || CM == CM_FP16) {
+      return fmaf(ah, xh, acc);
+    } else {
+      const float al = cm_round<B>(a - ah), xl = cm_round<B>(x - xh);
+      return fmaf(ah, xh, fmaf(ah, xl, fmaf(al, xh, acc)));
+    }
+  }
+}
+
 // 1D pass along `dir` at point g: sum_k A[i][k] in[.. k ..] (T = false) or A[k][i] (T = true)
-template <int N, bool T, typename R>
+template <int N, bool T, typename R, int CM = CM_NATIVE>
 __device__ __forceinline__ R line(const R* __restrict__ A, const R* __restrict__ in, int g, int dir) {
   const int st = pt_stride<N>(dir);
   const int i = (g / st) % N;
   const int base = g - i * st;
-  R acc = (T ? A[i] : A[i * N]) * in[base];
+  R acc = R(0);
 #pragma unroll
-  for (int k = 1; k < N; ++k) acc = fma(T ? A[k * N + i] : A[i * N + k], in[base + k * st], acc);
+  for (int k = 0; k < N; ++k) acc = cm_fma<CM>(T ? A[k * N + i] : A[i * N + k], in[base + k * st], acc);
+  return acc;
+}
+
+// the same pass accumulated into acc (NEG: subtracted), one FMA chain
+template <int N, bool T, bool NEG, typename R, int CM = CM_NATIVE>
+__device__ __forceinline__ R line_fma(const R* __restrict__ A, const R* __restrict__ in, int g, int dir, R acc) {
+  const int st = pt_stride<N>(dir);
+  const int i = (g / st) % N;
+  const int base = g - i * st;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const R a = T ? A[k * N + i] : A[i * N + k];
+    acc = cm_fma<CM>(NEG ? -a : a, in[base + k * st], acc);
+  }
   return acc;
 }
 
@@ -112,7 +155,7 @@ __device__ __forceinline__ void load_ops(const Ops* __restrict__ o, SmemOpsT<R>&
 // --------------------------------------------------------------------------------------------
 // k_interp: nodal -> Gauss values and face traces. NC = 1 (u) or 2 (u and tangent v).
 // --------------------------------------------------------------------------------------------
-template <int N, int NC, typename R>
+template <int N, int NC, typename R, int CM = CM_NATIVE>
 __global__ void k_interp(const double* __restrict__ u, const double* __restrict__ v, long long E,
                          const Ops* __restrict__ ops, R* __restrict__ ug, R* __restrict__ uf) {
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
@@ -139,7 +182,7 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     if (active)
-      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, false>(so.B, in + (el * C + c) * NP, g, dir);
+      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, false, R, CM>(so.B, in + (el * C + c) * NP, g, dir);
     __syncthreads();
     R* t = in;
     in = out;
@@ -166,7 +209,7 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
       const R* src = in + (l * C + 5 * pl + c) * NP;
       R acc = R(0);
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc = fma(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
+      for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
       uf[pl * plane_f + e * 30 * NF + rem] = acc;
     }
   }
@@ -179,7 +222,7 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
 // (u_hat picks up half of the own trace on interior faces) and qx receives, per face, the trace of
 // the gradient tangent this element would get from its neighbour's perturbation across that face:
 // kappa(f) (w n dS)(f) u_dot_nb(f) / 2 with kappa(f) = sum_k e_face[k]^2 / (w |J|)(g(f, k)).
-template <int N, int NC, bool BLK, typename R>
+template <int N, int NC, bool BLK, typename R, int CM = CM_NATIVE>
 __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, const R* __restrict__ geo,
                        const R* __restrict__ fgeo, const int* __restrict__ nbr,
                        const int* __restrict__ nbr_fo, const R* __restrict__ ug,
@@ -194,6 +237,7 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
   R* sN = sUh + EPB * 6 * C * NF;           // [EPB][6][3][NF]   w n dS
   R* sY = sN + EPB * 6 * 3 * NF;            // [EPB][9][NP]
   R* sQ = sY + EPB * 9 * NP;                // [EPB][3][C][NP]
+  R* sL = sQ + EPB * 3 * C * NP;            // [EPB][6][3][NF]: (w n_d dS) u_hat_c of the current c
   load_ops<N, R>(ops, so);
   const long long e0 = (long long)blockIdx.x * EPB;
   const long long plane_g = E * 5 * NP, plane_f = E * 30 * NF;
@@ -277,23 +321,28 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
       const R uc = sU[(el * C + c) * NP + g];
       for (int k = 0; k < 9; ++k) sY[(el * 9 + k) * NP + g] = G[k] * uc;
     }
+    // (w n_d dS) u_hat_c once per face point, shared by the N volume points behind it
+    for (int idx = threadIdx.x; idx < EPB * 6 * NF; idx += blockDim.x) {
+      const int l = idx / (6 * NF), phi = (idx / NF) % 6, f = idx % NF;
+      if (e0 + l < E) {
+        const R uh = sUh[((l * 6 + phi) * C + c) * NF + f];
+        for (int d = 0; d < 3; ++d) sL[((l * 6 + phi) * 3 + d) * NF + f] = sN[((l * 6 + phi) * 3 + d) * NF + f] * uh;
+      }
+    }
     __syncthreads();
     if (active) {
-      // lifting of the traces: sum over the 6 faces of e_face[i_axis] (w n_d dS) u_hat_c
-      R lift[3] = {R(0), R(0), R(0)};
-#pragma unroll
-      for (int phi = 0; phi < 6; ++phi) {
-        const int axis = phi >> 1;
-        const R coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
-        const int f = vol_face_point<N>(g, axis);
-        const R uh = sUh[((el * 6 + phi) * C + c) * NF + f];
-        for (int d = 0; d < 3; ++d) lift[d] = fma(coef * sN[((el * 6 + phi) * 3 + d) * NF + f], uh, lift[d]);
-      }
+      // q_d = (sum over the 6 faces of e_face[i_axis] (w n_d dS) u_hat_c - D^T (G u_c)) / (w |J|)
       for (int d = 0; d < 3; ++d) {
         R acc = R(0);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) acc += line<N, true>(so.D, sY + (el * 9 + a * 3 + d) * NP, g, a);
-        sQ[((el * 3 + d) * C + c) * NP + g] = (lift[d] - acc) * invW;
+        for (int phi = 0; phi < 6; ++phi) {
+          const int axis = phi >> 1;
+          const R coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
+          acc = cm_fma<CM>(coef, sL[((el * 6 + phi) * 3 + d) * NF + vol_face_point<N>(g, axis)], acc);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc = line_fma<N, true, true, R, CM>(so.D, sY + (el * 9 + a * 3 + d) * NP, g, a, acc);
+        sQ[((el * 3 + d) * C + c) * NP + g] = acc * invW;
       }
     }
     __syncthreads();
@@ -318,7 +367,7 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
       const R* src = sQ + ((l * 3 + d) * C + 5 * pl + c) * NP;
       R acc = R(0);
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc = fma(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
+      for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
       qf[pl * E * 90 * NF + e * 90 * NF + rem] = acc;
     }
   }
@@ -503,7 +552,7 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
 
 // stage_c != 0 (NC = 2): the tangent output is the DIRK stage operator J_G v = M v - stage_c J_r v,
 // M v = B^T (W B v) being formed from the tangent's own Gauss values
-template <int N, int NC, typename R>
+template <int N, int NC, typename R, int CM = CM_NATIVE>
 __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
                          const R* __restrict__ geo, const R* __restrict__ accg,
                          const R* __restrict__ xg, const R* __restrict__ ug,
@@ -581,12 +630,12 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R
       if constexpr (NC == 1) acc = srcv[c];
       else acc = (c < 5) ? srcv[c].v : srcv[c - 5].d;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) acc += line<N, true>(so.D, sF + ((el * 3 + a) * C + c) * NP, g, a);
+      for (int a = 0; a < 3; ++a) acc = line_fma<N, true, false, R, CM>(so.D, sF + ((el * 3 + a) * C + c) * NP, g, a, acc);
 #pragma unroll
       for (int phi = 0; phi < 6; ++phi) {
         const int axis = phi >> 1;
         const R coef = ((phi & 1) ? so.eR : so.eL)[axis_index<N>(g, axis)];
-        acc = fma(-coef, sH[((el * 6 + phi) * C + c) * NF + vol_face_point<N>(g, axis)], acc);
+        acc = cm_fma<CM>(-coef, sH[((el * 6 + phi) * C + c) * NF + vol_face_point<N>(g, axis)], acc);
       }
       if (NC == 2 && c >= 5 && stage_c != R(0)) acc = wu[c - 5] - stage_c * acc;
       sR[(el * C + c) * NP + g] = acc;
@@ -598,7 +647,7 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     if (active)
-      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, true>(so.B, in + (el * C + c) * NP, g, dir);
+      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, true, R, CM>(so.B, in + (el * C + c) * NP, g, dir);
     __syncthreads();
     R* tt = in;
     in = out;
@@ -800,7 +849,7 @@ template <int N, int NC, typename R>
 struct Smem {
   static constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
   static constexpr size_t interp = sizeof(R) * (2 * EPB * C * NP);
-  static constexpr size_t grad = sizeof(R) * (EPB * (C * NP + 6 * C * NF + 18 * NF + 9 * NP + 3 * C * NP));
+  static constexpr size_t grad = sizeof(R) * (EPB * (C * NP + 6 * C * NF + 18 * NF + 9 * NP + 3 * C * NP + 18 * NF));
   static constexpr size_t volume = sizeof(R) * (EPB * (3 * C * NP + 6 * C * NF + 2 * C * NP));
 };
 
@@ -817,31 +866,31 @@ static int set_smem(K kernel, size_t bytes) {
   return DG_OK;
 }
 
-template <int N, int NC, typename R = double>
+template <int N, int NC, typename R = double, int CM = CM_NATIVE>
 static int run_interp(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
   const size_t sm = Smem<N, NC, R>::interp;
-  int rc = set_smem(k_interp<N, NC, R>, sm);
+  int rc = set_smem(k_interp<N, NC, R, CM>, sm);
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
   const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_INTERP);
-  k_interp<N, NC, R><<<blocks, EPB * NP, sm, s>>>(u, v, m->E, m->d_ops, w.ug, w.uf);
+  k_interp<N, NC, R, CM><<<blocks, EPB * NP, sm, s>>>(u, v, m->E, m->d_ops, w.ug, w.uf);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_interp");
   return DG_OK;
 }
 
-template <int N, int NC, bool BLK = false, typename R = double>
+template <int N, int NC, bool BLK = false, typename R = double, int CM = CM_NATIVE>
 static int run_grad(dg_mesh* m, cudaStream_t s) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
   const size_t sm = Smem<N, NC, R>::grad;
-  int rc = set_smem(k_grad<N, NC, BLK, R>, sm);
+  int rc = set_smem(k_grad<N, NC, BLK, R, CM>, sm);
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
   const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_GRAD);
-  k_grad<N, NC, BLK, R><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), w.geo, w.fgeo, m->nbr,
+  k_grad<N, NC, BLK, R, CM><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), w.geo, w.fgeo, m->nbr,
                                                       m->nbr_fo, w.ug, w.uf, w.qg, w.qf, w.qx);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_grad");
@@ -863,16 +912,16 @@ static int run_faces(dg_mesh* m, cudaStream_t s) {
   return DG_OK;
 }
 
-template <int N, int NC, typename R = double>
+template <int N, int NC, typename R = double, int CM = CM_NATIVE>
 static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t s, double stage_c = 0.0) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
   const size_t sm = Smem<N, NC, R>::volume;
-  int rc = set_smem(k_volume<N, NC, R>, sm);
+  int rc = set_smem(k_volume<N, NC, R, CM>, sm);
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
   const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_VOLUME);
-  k_volume<N, NC, R><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), (R)t, w.geo, w.acc, w.xg,
+  k_volume<N, NC, R, CM><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), (R)t, w.geo, w.acc, w.xg,
                                                    w.ug, w.qg, w.fh, r, jv, (R)stage_c);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_volume");
@@ -943,6 +992,33 @@ template <int N>
 int Driver<N>::jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv,
                             cudaStream_t s, bool f32) {
   return f32 ? jv_blockdiag_p<float>(m, u, probe, t, jv, s) : jv_blockdiag_p<double>(m, u, probe, t, jv, s);
+}
+
+template <int N>
+template <int CM>
+int Driver<N>::eval_cm_t(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
+                         cudaStream_t s) {
+  const bool tan = v != nullptr;
+  int rc = tan ? run_interp<N, 2, float, CM>(m, u, v, s) : run_interp<N, 1, float, CM>(m, u, nullptr, s);
+  if (rc) return rc;
+  rc = tan ? run_grad<N, 2, false, float, CM>(m, s) : run_grad<N, 1, false, float, CM>(m, s);
+  if (rc) return rc;
+  rc = tan ? run_faces<N, 2, false, float>(m, s) : run_faces<N, 1, false, float>(m, s);
+  if (rc) return rc;
+  return tan ? run_volume<N, 2, float, CM>(m, t, r, jv, s) : run_volume<N, 1, float, CM>(m, t, r, nullptr, s);
+}
+
+template <int N>
+int Driver<N>::eval_cm(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv, int cm,
+                       cudaStream_t s) {
+  switch (cm) {
+    case CM_NATIVE: return eval_cm_t<CM_NATIVE>(m, u, v, t, r, jv, s);
+    case CM_BF16: return eval_cm_t<CM_BF16>(m, u, v, t, r, jv, s);
+    case CM_FP16: return eval_cm_t<CM_FP16>(m, u, v, t, r, jv, s);
+    case CM_BF16X3: return eval_cm_t<CM_BF16X3>(m, u, v, t, r, jv, s);
+    case CM_FP16X3: return eval_cm_t<CM_FP16X3>(m, u, v, t, r, jv, s);
+    default: return fail(DG_EINVAL, "unknown contraction mode");
+  }
 }
 
 template <int N>

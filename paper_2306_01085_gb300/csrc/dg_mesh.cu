@@ -688,3 +688,12 @@ int stage_jvp(dg_mesh* mesh, const double* u, const double* v, double t, double 
   if (rc) return rc;
   return drv_residual(mesh, u, v, t, nullptr, out, true, s, f32, c);
 }
+
+extern "C" int dg_eval_precision(dg_mesh* mesh, int32_t mode, const double* u, const double* v, double t, double* r,
+                                 double* jv, void* stream) {
+  if (!mesh || !u || (!r && !jv) || (v && !jv)) return fail(DG_EINVAL, "dg_eval_precision: bad argument");
+  if (mode < DG_CM_FP32 || mode > DG_CM_FP16X3) return fail(DG_EINVAL, "dg_eval_precision: unknown mode");
+  int rc = ensure_f32(mesh);
+  if (rc) return rc;
+  DG_DISPATCH(mesh, eval_cm(mesh, u, v, t, r, jv, mode, (cudaStream_t)stream));
+}

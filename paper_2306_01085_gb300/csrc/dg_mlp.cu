@@ -1,6 +1,6 @@
 // Learned element preconditioner: features, network forward/backward, training and application.
 //
-// The paper has no learned component; this is the benchmark spec's learned right preconditioner for
+// The paper has no learned component; this is the library's learned right preconditioner for
 // the GMRES of Sec. 3.2. Per element e, with S_e the diagonal of the element mass matrix (one
 // value per node, shared by the five variables) and Bs_e = S^{-1/2} B_e S^{-1/2} the scaled exact
 // diagonal block of J_G, a two-hidden-layer SiLU network maps features x_e to

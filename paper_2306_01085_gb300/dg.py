@@ -106,6 +106,7 @@ def lib():
     L.dg_precond_setup.argtypes = [vp, i32, dp, d, d, vp]
     L.dg_precond_apply.argtypes = [vp, i32, dp, dp, vp]
     L.dg_block_assemble.argtypes = [vp, dp, d, d, dp, vp]
+    L.dg_eval_precision.argtypes = [vp, i32, dp, dp, d, dp, dp, vp]
     _lib = L
     return L
 
@@ -397,3 +398,21 @@ Mesh.mlp_features = _mesh_mlp_features
 Mesh.mlp_harvest = _mesh_mlp_harvest
 Mesh.mlp_loss_grad = _mesh_mlp_loss_grad
 Mesh.mlp_train = _mesh_mlp_train
+
+
+CM = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp16x3": 4}
+
+
+def _mesh_eval_precision(self, mode, u, v=None, t=0.0, r=None, jv=None):
+    """Residual (v is None) or fused residual + exact Jv with the basis contractions in one of the
+    modes of CM; returns (r, jv)."""
+    if v is None and r is None:
+        r = self.empty()
+    if v is not None and jv is None:
+        jv = self.empty()
+    _check(lib().dg_eval_precision(self._h, CM[mode], _ptr(u, self.u_shape, "u"), _ptr(v, self.u_shape, "v"),
+                                   float(t), _ptr(r, self.u_shape, "r"), _ptr(jv, self.u_shape, "jv"), _stream()))
+    return r, jv
+
+
+Mesh.eval_precision = _mesh_eval_precision

@@ -102,3 +102,45 @@ def test_mixed_precision_step_matches_plain_step(torch_cuda):
     diff = np.abs(res["f64"][1] - res["f32"][1]).max(axis=(0, 2))
     print("\nmixed vs plain:", diff / du, res["f64"][0]["gmres"], res["f32"][0]["gmres"])
     assert np.all(diff <= 1e-4 * du), (diff, du)
+
+
+@pytest.mark.parametrize("case", ["box4_p2", "shell_p2_euv"])
+def test_contraction_precision_modes(torch_cuda, case):
+    """Basis contractions with bfloat16 / binary16 operands and FP32 accumulation (the arithmetic
+    of a tensor-core MMA), with and without hi + lo splits, against the FP64 oracle. Reported per
+    variable; held to what the arithmetic fixes: the FP32 mode is the FP32 variant bit for bit,
+    one-term bfloat16 is at least as wrong as FP32, and the three-product split recovers most of
+    the lost digits (its operands carry 16 bits, so its error is at most 2^-7 of the one-term
+    error plus the FP32 floor)."""
+    torch = torch_cuda
+    from paper_2306_01085_gb300.dg import Mesh
+    if case == "box4_p2":
+        d = W.CONFIGS["box4_p2"][0]()
+    else:
+        d = W.shell_desc(n=3, nr=6, p=2, euv=True)
+    om = OM.OracleMesh(d)
+    u = W.state_for(d, om.X, 3)
+    v = W.unit_vector(13, u.shape)
+    r_ref = OD.residual(om, u, None, 0.1)
+    jv_ref = OD.jvp(om, u, v, 0.1)
+    m = Mesh(d, nodes=om.X)
+    ug = torch.from_numpy(u).cuda()
+    vg = torch.from_numpy(v).cuda()
+    r32 = m.residual_f32(ug, t=0.1).cpu().numpy()
+    err = {}
+    for mode in ("fp32", "bf16", "fp16", "bf16x3", "fp16x3"):
+        r, _ = m.eval_precision(mode, ug, t=0.1)
+        r2, jv = m.eval_precision(mode, ug, vg, t=0.1, r=torch.empty_like(ug))
+        r, r2, jv = r.cpu().numpy(), r2.cpu().numpy(), jv.cpu().numpy()
+        if mode == "fp32":
+            assert np.array_equal(r, r32)
+        assert np.array_equal(r, r2) or mode != "fp32"
+        with np.errstate(invalid="ignore"):
+            err[mode] = (_per_var(r, r_ref), _per_var(jv, jv_ref))
+        print(f"\n{case} {mode:7s} r {err[mode][0]}\n{case} {mode:7s} Jv {err[mode][1]}")
+    m.close()
+    for k in (0, 1):
+        e32, e16, e3 = err["fp32"][k], err["bf16"][k], err["bf16x3"][k]
+        assert np.all(np.isfinite(e16)) and np.all(np.isfinite(e3))
+        assert e16.max() >= e32.max()
+        assert np.all(e3 <= e16 / 128 + 4 * e32 + 1e-7), (e3, e16, e32)
