@@ -382,6 +382,9 @@ def main_implicit(args):
     plain_none: FP64 unpreconditioned GMRES(30)
     mixed_mlp:  mixed precision with the learned diagonal + low-rank preconditioner, trained first on
                 the exact blocks of --mlp-steps plain steps (training time reported separately)
+    mixed_rb_bj: mixed precision, the reduced basis of the last 8 Newton updates (Sec. 3.2) over
+                block-Jacobi, with the RB initial guess
+    mixed_rb:   mixed precision, the reduced basis over the mass matrix (nothing assembled)
     Every variant starts from the same state; the final states are compared with plain_bj.
     """
     import numpy as np
@@ -403,6 +406,8 @@ def main_implicit(args):
         "plain_none": dict(precond="none", jv_prec="f64"),
     }
     variants["mixed_mlp"] = dict(precond="mlp", jv_prec="f32")
+    variants["mixed_rb_bj"] = dict(precond="rb_bj", jv_prec="f32")
+    variants["mixed_rb"] = dict(precond="rb", jv_prec="f32")
     results, finals = {}, {}
     training = None
     if "mixed_mlp" in args.variants.split(","):
@@ -428,6 +433,7 @@ def main_implicit(args):
     for name in args.variants.split(","):
         kw = variants[name]
         u = u0.clone()
+        mesh.rb_reset()
         steps = []
         rc = 0
         kernels = None
@@ -466,7 +472,7 @@ def main_implicit(args):
     out = {"metric": "implicit DIRK(3,3) step wall time at Newton 1e-8", "unit": "s/step", "config": config,
            "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "dt_s": 60.0, "steps": args.steps, "variants": results,
            "mlp_training": training}
-    for name in ("mixed_bj", "mixed_mlp"):
+    for name in ("mixed_bj", "mixed_mlp", "mixed_rb_bj", "mixed_rb"):
         if base and results.get(name, {}).get("rc") == 0:
             out[f"speedup_{name}_vs_plain_bj"] = round(np.mean(base) / np.mean(results[name]["wall_s_per_step"]), 3)
     print(json.dumps(out), flush=True)

@@ -164,6 +164,10 @@ int dg_eval_precision(dg_mesh* mesh, int32_t mode, const double* u, const double
 
 /* Mass matrix product (M v)_i = sum_j (phi_i, phi_j) v_j per element and variable (Sec. 3.1). */
 int dg_mass_apply(dg_mesh* mesh, const double* v, double* mv, void* stream);
+/* Inverse mass matrix product M^{-1} v, element by element: with (p+1)^3 Gauss points the nodal
+ * mass matrix factors as B^T W B (B the square GLL-to-Gauss interpolation, W = w |J|), so
+ * M^{-1} = B^{-1} W^{-1} B^{-T} (three 1D passes each way). v and mv may alias. */
+int dg_mass_inverse_apply(dg_mesh* mesh, const double* v, double* mv, void* stream);
 
 /*
  * The residual of dg_residual (q computed from u) for callers that must not have the library
@@ -189,6 +193,8 @@ int dg_residual_static(dg_mesh* mesh, const double* u, double t, double* r, void
 #define DG_PC_NONE 0         /* no preconditioner */
 #define DG_PC_BJ   1         /* exact element diagonal blocks of J_G, FP32 inverses (block-Jacobi) */
 #define DG_PC_MLP  2         /* learned diagonal + low-rank inverse per element */
+#define DG_PC_RB   3         /* reduced basis of the last Newton updates over the mass matrix (Sec. 3.2) */
+#define DG_PC_RB_BJ 4        /* reduced basis over block-Jacobi */
 
 #define DG_REFRESH_STEP   0  /* build the preconditioner once per step, at u_n */
 #define DG_REFRESH_STAGE  1  /* rebuild at the start of every stage */
@@ -211,6 +217,8 @@ typedef struct dg_solver_opts {
     double newton_rtol;      /* stop when ||G||_2 <= newton_rtol ||G(U^0)||_2 (1e-8) */
     double gmres_rtol;       /* each Newton system to ||b - J x|| <= gmres_rtol ||b|| (1e-3) */
     double abs_floor;        /* or when ||G||_2 <= abs_floor ||M U||_2 (1e-14) */
+    int32_t rb_size;         /* DG_PC_RB*: Newton updates kept in the reduced basis, 1..16 (8) */
+    int32_t reserved;        /* zero */
 } dg_solver_opts;
 
 typedef struct dg_step_stats {
@@ -224,7 +232,7 @@ typedef struct dg_step_stats {
 } dg_step_stats;
 
 /* Defaults: 3 stages, GMRES(30), 10 cycles, 20 Newton iterations, no preconditioner, exact Jv,
- * Newton 1e-8 relative, GMRES 1e-3 relative, floor 1e-14. */
+ * Newton 1e-8 relative, GMRES 1e-3 relative, floor 1e-14, reduced basis of 8 updates. */
 void dg_solver_opts_default(dg_solver_opts* opts);
 
 /* The DIRK tableau the step uses, derived from the order conditions: a [stages][stages] row-major,
@@ -260,6 +268,35 @@ int dg_precond_setup(dg_mesh* mesh, int32_t kind, const double* u, double t, dou
 
 /* y = P^{-1} x with the preconditioner last built (x, y FP64 [n_elem][5][n_p]; may alias). */
 int dg_precond_apply(dg_mesh* mesh, int32_t kind, const double* x, double* y, void* stream);
+
+/*
+ * Reduced-basis preconditioner and initial guess (Sec. 3.2). The RB space W is the span of the last
+ * rb_size Newton updates, kept by dg_implicit_step as a rolling window over Newton iterations,
+ * stages and steps (it survives between calls until dg_rb_reset). At every Newton iteration the
+ * window is orthonormalised (classical Gram-Schmidt twice, updates within 1e-10 of the span of the
+ * others dropped), Z = J_G W is formed with the step's Jv mode and precision, and GMRES is
+ * right-preconditioned with the inverse of
+ *     J~ = P0 + (Z - P0 W) W^T,
+ * which equals J_G on the RB space and the base P0 on its orthogonal complement: P0 = M (the
+ * element mass matrix, DG_PC_RB, nothing assembled) or the block-Jacobi blocks (DG_PC_RB_BJ, built
+ * as DG_PC_BJ is, per precond_refresh). Applied by the Woodbury identity,
+ *     J~^{-1} x = P0^{-1} x - (P0^{-1} Z - W) (W^T P0^{-1} Z)^{-1} W^T P0^{-1} x,
+ * i.e. one base solve, rb_size dot products and axpys. GMRES starts from the RB least-squares
+ * guess x0 = W a, a = argmin ||b - Z a||_2, when it reduces the residual. With an empty window
+ * J~ = P0 and x0 = 0.
+ */
+
+/* Replace the window by the r vectors w ([r][n_elem][5][n_p], device, r <= 16) and build the RB
+ * preconditioner of J_G = M - dt_aii J_r(u) at (u, t) with exact FP64 Jv; base DG_PC_RB or
+ * DG_PC_RB_BJ (which also builds the block-Jacobi blocks at u). dg_precond_apply with the same
+ * kind then applies J~^{-1}. Synchronises the stream. */
+int dg_rb_load(dg_mesh* mesh, const double* w, int32_t r, const double* u, double t, double dt_aii, int32_t base,
+               void* stream);
+/* x0 = W a, a = argmin ||b - Z a||_2 with the RB preconditioner last built (x0 = 0 when the space
+ * is empty or the guess does not reduce ||b||). Synchronises the stream. */
+int dg_rb_initial_guess(dg_mesh* mesh, const double* b, double* x0, void* stream);
+/* Empty the window (the next implicit step starts without a reduced basis). */
+int dg_rb_reset(dg_mesh* mesh);
 
 /* Assemble the exact diagonal blocks of J_G = M - dt_aii J_r(u) (the ones DG_PC_BJ factors) into a
  * caller device buffer out, FP32 [n_elem][5 n_p][5 n_p], each block column-major (out[e][j][i] =

@@ -162,6 +162,7 @@ struct Driver {
   static int q_to_nodal(dg_mesh* m, double* q, cudaStream_t s);
   static int q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s);
   static int mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
+  static int mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
   // J_r probe restricted to each element's own diagonal block (exact, one column per element)
   static int jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s,
                           bool f32 = false);

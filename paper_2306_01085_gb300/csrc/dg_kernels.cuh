@@ -731,6 +731,54 @@ __global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, co
   }
 }
 
+// M^{-1} v = B^{-1} (w |J|)^{-1} B^{-T} v for the 5 variables of EPB elements per CTA (the nodal
+// mass matrix is B^T W B with B the square GLL-to-Gauss interpolation); in place allowed
+template <int N>
+__global__ void k_mass_inv(long long E, const Ops* __restrict__ ops, const double* in_g, double* out_g,
+                           const double* __restrict__ geo) {
+  constexpr int NP = Shape<N>::NP, EPB = Epb<N, 1>::value, C = 5;
+  __shared__ SmemOps so;
+  extern __shared__ double smem[];
+  double* b0 = smem;                 // [EPB][C][NP]
+  double* b1 = smem + EPB * C * NP;  // [EPB][C][NP]
+  load_ops<N, double>(ops, so);
+  const long long e0 = (long long)blockIdx.x * EPB;
+  for (int idx = threadIdx.x; idx < EPB * C * NP; idx += blockDim.x) {
+    const long long e = e0 + idx / (C * NP);
+    if (e < E) b0[idx] = in_g[e0 * C * NP + idx];
+  }
+  __syncthreads();
+  const int el = threadIdx.x / NP, g = threadIdx.x % NP;
+  const bool active = el < EPB && (e0 + el) < E;
+  double* in = b0;
+  double* out = b1;
+  for (int dir = 0; dir < 3; ++dir) {   // B^{-T}
+    if (active)
+      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, true>(so.Binv, in + (el * C + c) * NP, g, dir);
+    __syncthreads();
+    double* tt = in;
+    in = out;
+    out = tt;
+  }
+  if (active) {
+    const double iw = 1.0 / geo[(e0 + el) * 10 * NP + 9 * NP + g];
+    for (int c = 0; c < C; ++c) in[(el * C + c) * NP + g] *= iw;
+  }
+  __syncthreads();
+  for (int dir = 0; dir < 3; ++dir) {   // B^{-1}
+    if (active)
+      for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, false>(so.Binv, in + (el * C + c) * NP, g, dir);
+    __syncthreads();
+    double* tt = in;
+    in = out;
+    out = tt;
+  }
+  for (int idx = threadIdx.x; idx < EPB * C * NP; idx += blockDim.x) {
+    const long long e = e0 + idx / (C * NP);
+    if (e < E) out_g[e0 * C * NP + idx] = in[idx];
+  }
+}
+
 // --------------------------------------------------------------------------------------------
 // geometry at Gauss points and face points (isoparametric map of the node coordinates)
 // --------------------------------------------------------------------------------------------
@@ -1048,6 +1096,20 @@ int Driver<N>::q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) {
                                                                                    nullptr, m->ws.qf);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_tensor(q gauss)");
+  return DG_OK;
+}
+
+template <int N>
+int Driver<N>::mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s) {
+  constexpr int NP = Shape<N>::NP;
+  constexpr int EPB = Epb<N, 1>::value;
+  const size_t sm = sizeof(double) * 2 * EPB * 5 * NP;
+  int rc = set_smem(k_mass_inv<N>, sm);
+  if (rc) return rc;
+  prof_begin(m, s, KK_TENSOR);
+  k_mass_inv<N><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, v, mv, m->geo);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_mass_inv");
   return DG_OK;
 }
 

@@ -40,6 +40,9 @@ static int drv_residual(dg_mesh* m, const double* u, const double* v, double t, 
 static int drv_q_to_nodal(dg_mesh* m, double* q, cudaStream_t s) { DG_DISPATCH(m, q_to_nodal(m, q, s)); }
 static int drv_q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) { DG_DISPATCH(m, q_from_nodal(m, q, s)); }
 static int drv_mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s) { DG_DISPATCH(m, mass(m, v, mv, s)); }
+static int drv_mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s) {
+  DG_DISPATCH(m, mass_inv(m, v, mv, s));
+}
 
 // ------------------------------------------------------------------------------------------
 // radial layers with geometric growth from the first-layer height (Sec. 3.3)
@@ -599,6 +602,11 @@ extern "C" int dg_jvp(dg_mesh* mesh, const double* u, const double* v, double t,
 extern "C" int dg_mass_apply(dg_mesh* mesh, const double* v, double* mv, void* stream) {
   if (!mesh || !v || !mv) return fail(DG_EINVAL, "dg_mass_apply: null argument");
   return drv_mass(mesh, v, mv, (cudaStream_t)stream);
+}
+
+extern "C" int dg_mass_inverse_apply(dg_mesh* mesh, const double* v, double* mv, void* stream) {
+  if (!mesh || !v || !mv) return fail(DG_EINVAL, "dg_mass_inverse_apply: null argument");
+  return drv_mass_inv(mesh, v, mv, (cudaStream_t)stream);
 }
 
 static const char* kKernelNames[KK_COUNT] = {"k_interp", "k_grad", "k_faces", "k_volume", "k_tensor", "k_blas",

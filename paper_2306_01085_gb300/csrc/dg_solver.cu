@@ -106,6 +106,7 @@ static int dirk_tableau(int stages, double A[3][3], double c[3]) {
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 constexpr int RED_THREADS = 256;
 constexpr int MAXK = 64;          // largest restart + 1
+constexpr int RB_MAX = 16;        // largest reduced basis
 
 __global__ void k_lincomb(long long n, double a, const double* __restrict__ x, double b,
                           const double* __restrict__ y, double c, const double* __restrict__ z,
@@ -138,13 +139,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(long long n, int k, const 
     double acc[MDOT_G];
 #pragma unroll
     for (int j = 0; j < MDOT_G; ++j) acc[j] = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-      const double wi = w[i];
+    // two elements per thread per pass keep twice the loads in flight
+    const long long T = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * T) {
+      const long long i2 = i + T;
+      const bool ok2 = i2 < n;
+      const double wa = w[i], wb = ok2 ? w[i2] : 0.0;
 #pragma unroll
       for (int j = 0; j < MDOT_G; ++j) {
         const int jj = j0 + j;
-        if (jj < k) acc[j] = fma(V[jj * ldv + i], wi, acc[j]);
-        else if (jj == k) acc[j] = fma(wi, wi, acc[j]);
+        if (jj < k) {
+          const double* Vj = V + jj * ldv;
+          acc[j] = fma(Vj[i], wa, acc[j]);
+          if (ok2) acc[j] = fma(Vj[i2], wb, acc[j]);
+        } else if (jj == k) {
+          acc[j] = fma(wa, wa, acc[j]);
+          acc[j] = fma(wb, wb, acc[j]);
+        }
       }
     }
 #pragma unroll
@@ -160,6 +171,157 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(long long n, int k, const 
       partial[(j0 + threadIdx.x) * RED_BLOCKS + blockIdx.x] = v;
     }
     __syncthreads();
+  }
+}
+
+// Fused Gram-Schmidt sweep: w <- w - sum_{j<k} h_j V_j, then (DOTS) partial[j][block] =
+// sum_i V_j[i] w[i] for j < k, and partial[DOTS ? k : 0][block] = sum_i w[i]^2. V_j[i] is read
+// from HBM once; the dot pass re-reads it right after the update (L1/L2 hits). KM >= k.
+template <int KM, bool DOTS>
+__global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot(long long n, int k, const double* __restrict__ V,
+                                                              long long ldv, const double* __restrict__ h,
+                                                              double* __restrict__ w, double* __restrict__ partial) {
+  constexpr int NA = DOTS ? KM + 1 : 1;
+  __shared__ double hs[KM];
+  __shared__ double red[RED_THREADS / 32][NA];
+  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double acc[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) acc[j] = 0.0;
+  const long long T = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += T) {
+    double x = w[i];
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) x = fma(-hs[j], V[j * ldv + i], x);
+    w[i] = x;
+    if constexpr (DOTS) {
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (j < k) acc[j] = fma(V[j * ldv + i], x, acc[j]);
+    }
+    acc[NA - 1] = fma(x, x, acc[NA - 1]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    double v = acc[j];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < NA; j += blockDim.x) {
+    if (DOTS && j < KM && j >= k) continue;
+    double v = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) v += red[q][j];
+    const int row = DOTS ? (j == KM ? k : j) : 0;
+    partial[row * RED_BLOCKS + blockIdx.x] = v;
+  }
+}
+
+// The same two operations for a compile-time number of vectors K and 16-byte loads (n even, so
+// every V_j starts on a 16-byte boundary): no predication, every load of an element issued
+// back to back. partial rows as above.
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot_k(long long n2, const double2* __restrict__ V, long long ldv2,
+                                                       const double2* __restrict__ w, double* __restrict__ partial) {
+  double acc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) acc[j] = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double2 x = w[i];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const double2 v = V[j * ldv2 + i];
+      acc[j] = fma(v.x, x.x, fma(v.y, x.y, acc[j]));
+    }
+    acc[K] = fma(x.x, x.x, fma(x.y, x.y, acc[K]));
+  }
+  __shared__ double red[RED_THREADS / 32][K + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    double v = acc[j];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j <= K; j += blockDim.x) {
+    double v = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) v += red[q][j];
+    partial[j * RED_BLOCKS + blockIdx.x] = v;
+  }
+}
+
+template <int K, bool DOTS>
+__global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot_k(long long n2, const double2* __restrict__ V,
+                                                                long long ldv2, const double* __restrict__ h,
+                                                                double2* __restrict__ w, double* __restrict__ partial) {
+  // K <= 8: the element's V values stay in registers for the dots. K > 8: vector loops unrolled
+  // by 8, the dot pass reads V again from L2 (ld.global.cg), and each thread's K dot accumulators
+  // live in dynamic shared memory laid out [j][thread] (conflict-free), so nothing spills.
+  constexpr bool SMALL = K <= 8;
+  constexpr bool SACC = DOTS && !SMALL;
+  constexpr int NR = (DOTS && SMALL) ? K + 1 : 1;   // register accumulators (last: |w|^2)
+  extern __shared__ double sacc[];                  // SACC: [K][RED_THREADS]
+  __shared__ double hs[K > 0 ? K : 1];
+  if (threadIdx.x < K) hs[threadIdx.x] = h[threadIdx.x];
+  if constexpr (SACC)
+    for (int j = 0; j < K; ++j) sacc[j * RED_THREADS + threadIdx.x] = 0.0;
+  __syncthreads();
+  double acc[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) acc[j] = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    double2 x = w[i];
+    if constexpr (SMALL) {
+      double2 v[K > 0 ? K : 1];
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        v[j] = V[j * ldv2 + i];
+        x.x = fma(-hs[j], v[j].x, x.x);
+        x.y = fma(-hs[j], v[j].y, x.y);
+      }
+      w[i] = x;
+      if constexpr (DOTS) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc[j] = fma(v[j].x, x.x, fma(v[j].y, x.y, acc[j]));
+      }
+    } else {
+#pragma unroll 8
+      for (int j = 0; j < K; ++j) {
+        const double2 vj = V[j * ldv2 + i];
+        x.x = fma(-hs[j], vj.x, x.x);
+        x.y = fma(-hs[j], vj.y, x.y);
+      }
+      w[i] = x;
+      if constexpr (DOTS) {
+#pragma unroll 8
+        for (int j = 0; j < K; ++j) {
+          const double2 vj = __ldcg(&V[j * ldv2 + i]);
+          double& a = sacc[j * RED_THREADS + threadIdx.x];
+          a = fma(vj.x, x.x, fma(vj.y, x.y, a));
+        }
+      }
+    }
+    acc[NR - 1] = fma(x.x, x.x, fma(x.y, x.y, acc[NR - 1]));
+  }
+  constexpr int NA = DOTS ? K + 1 : 1;
+  __shared__ double red[RED_THREADS / 32][NA];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = 0; j < NA; ++j) {
+    double a;
+    if constexpr (SACC) a = (j < K) ? sacc[j * RED_THREADS + threadIdx.x] : acc[0];
+    else a = (NR == 1) ? acc[0] : acc[j < NR ? j : NR - 1];
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) red[warp][j] = a;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < NA; j += blockDim.x) {
+    double a = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) a += red[q][j];
+    partial[j * RED_BLOCKS + blockIdx.x] = a;
   }
 }
 
@@ -183,6 +345,16 @@ __global__ void k_maxpy(long long n, int k, const double* __restrict__ V, long l
     for (int j = 0; j < k; ++j) v = fma(-hs[j], V[j * ldv + i], v);
     w[i] = v;
   }
+}
+
+// t = C s for the r x r row-major matrix C (reduced-basis coefficients)
+__global__ void k_small_matvec(int r, const double* __restrict__ C, const double* __restrict__ sv,
+                               double* __restrict__ tv) {
+  const int i = threadIdx.x;
+  if (i >= r) return;
+  double acc = 0.0;
+  for (int j = 0; j < r; ++j) acc = fma(C[i * r + j], sv[j], acc);
+  tv[i] = acc;
 }
 
 // out = sum_j y[j] V_j (j < k)
@@ -341,12 +513,23 @@ struct Solver {
   double* vec = nullptr;    // named work vectors below, [NV][n]
   double* partial = nullptr;
   double* hdev = nullptr;   // [2][MAXK]
-  double* hhost = nullptr;  // pinned [2][MAXK]
+  double* hhost = nullptr;  // pinned [2 MAXK + RB_MAX^2]
   double* probe = nullptr;  // [n]
   float* blocks = nullptr;  // [E][5Np][5Np]: assembled blocks, then (in place) their inverses
   int* piv = nullptr;
   int* info = nullptr;
   bool bj_ready = false;
+  // reduced basis (Sec. 3.2): ring of the last Newton updates, orthonormal basis W, Z = J_G W,
+  // Y = P0^{-1} Z - W, C = (W^T P0^{-1} Z)^{-1} on the device, Gram Z^T Z on the host
+  int rb_cap = 0, rb_count = 0, rb_head = 0, rb_r = 0, rb_kind = 0;
+  bool rb_ready = false;
+  double* rb_ring = nullptr;
+  double* rb_W = nullptr;
+  double* rb_Z = nullptr;
+  double* rb_Y = nullptr;
+  double* rb_C = nullptr;   // [RB_MAX * RB_MAX]
+  double* rb_s = nullptr;   // [2 RB_MAX]
+  std::vector<double> rb_gram;
   static constexpr int NV = 12;
   double* v(int i) { return vec + (long long)i * n; }
 };
@@ -355,7 +538,8 @@ enum { VU = 0, VKNOWN, VR0, VR1, VR2, VG, VRES, VZ, VW, VDU, VTMP, VUN };
 
 static void solver_free(Solver* S) {
   if (!S) return;
-  void* ptrs[] = {S->V, S->vec, S->partial, S->hdev, S->probe, S->blocks, S->piv, S->info};
+  void* ptrs[] = {S->V, S->vec, S->partial, S->hdev, S->probe, S->blocks, S->piv, S->info,
+                  S->rb_ring, S->rb_W, S->rb_Z, S->rb_Y, S->rb_C, S->rb_s};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (S->hhost) cudaFreeHost(S->hhost);
@@ -386,7 +570,7 @@ static int solver_get(dg_mesh* m, int restart, Solver** out) {
   if (err == cudaSuccess) err = cudaMalloc(&S->vec, sizeof(double) * (size_t)Solver::NV * S->n);
   if (err == cudaSuccess) err = cudaMalloc(&S->partial, sizeof(double) * RED_BLOCKS * MAXK);
   if (err == cudaSuccess) err = cudaMalloc(&S->hdev, sizeof(double) * 2 * MAXK);
-  if (err == cudaSuccess) err = cudaMallocHost(&S->hhost, sizeof(double) * 2 * MAXK);
+  if (err == cudaSuccess) err = cudaMallocHost(&S->hhost, sizeof(double) * (2 * MAXK + RB_MAX * RB_MAX));
   if (err != cudaSuccess) {
     solver_free(S);
     return fail(DG_ENOMEM, std::string("solver storage: ") + cudaGetErrorString(err));
@@ -422,6 +606,63 @@ static unsigned grid_for(long long n) {
   return (unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
 }
 
+#define DG_K_CASES(X)                                                                                   \
+  X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18)    \
+  X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
+
+// partial rows 0..k-1 = V^T w, row k = |w|^2 (k vectors of length n, leading dimension n)
+static void mdot(long long n, int k, const double* V, const double* w, double* partial, cudaStream_t s) {
+  if (n % 2 == 0 && k <= 32) {
+    const long long n2 = n / 2;
+    const double2* V2 = reinterpret_cast<const double2*>(V);
+    const double2* w2 = reinterpret_cast<const double2*>(w);
+    switch (k) {
+#define DG_MD(K) \
+  case K: k_mdot_k<K><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V2, n2, w2, partial); return;
+      DG_K_CASES(DG_MD)
+#undef DG_MD
+    }
+  }
+  k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, V, n, w, partial);
+}
+
+// w <- w - V h (k vectors); partial rows: DOTS ? (V^T w, |w|^2 at row k) : |w|^2 at row 0
+static void update_dot(long long n, int k, const double* V, const double* h, double* w, double* partial, bool dots,
+                       cudaStream_t s) {
+  if (n % 2 == 0 && k >= 1 && k <= 32) {
+    const long long n2 = n / 2;
+    const double2* V2 = reinterpret_cast<const double2*>(V);
+    double2* w2 = reinterpret_cast<double2*>(w);
+    switch (k) {
+#define DG_UDK(K)                                                                                            \
+  case K:                                                                                                    \
+    if (dots) {                                                                                              \
+      const int sm = K > 8 ? (int)sizeof(double) * K * RED_THREADS : 0;                                      \
+      static bool attr = false;                                                                              \
+      if (!attr && sm > 0)                                                                                   \
+        cudaFuncSetAttribute(k_update_dot_k<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);      \
+      attr = true;                                                                                           \
+      k_update_dot_k<K, true><<<RED_BLOCKS, RED_THREADS, sm, s>>>(n2, V2, n2, h, w2, partial);               \
+    } else {                                                                                                 \
+      k_update_dot_k<K, false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V2, n2, h, w2, partial);               \
+    }                                                                                                        \
+    return;
+      DG_K_CASES(DG_UDK)
+#undef DG_UDK
+    }
+  }
+#define DG_UD(KM)                                                                                        \
+  do {                                                                                                   \
+    if (dots) k_update_dot<KM, true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, V, n, h, w, partial);      \
+    else k_update_dot<KM, false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, V, n, h, w, partial);          \
+  } while (0)
+  if (k <= 8) DG_UD(8);
+  else if (k <= 16) DG_UD(16);
+  else if (k <= 32) DG_UD(32);
+  else DG_UD(64);
+#undef DG_UD
+}
+
 // J_G v = M v - c J_r(U) v
 static int stage_matvec(dg_mesh* m, Solver* S, const double* U, double t, double c, int jv_mode, int jv_prec,
                         const double* v, double* out, cudaStream_t s) {
@@ -442,7 +683,7 @@ static int stage_matvec(dg_mesh* m, Solver* S, const double* U, double t, double
 // squared 2-norm on the device, read back (synchronises the stream)
 static int norm2(dg_mesh* m, Solver* S, const double* x, double* out, cudaStream_t s) {
   prof_begin(m, s, KK_BLAS);
-  k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(S->n, 0, S->V, S->n, x, S->partial);
+  mdot(S->n, 0, S->V, x, S->partial, s);
   k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev, 0);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_mdot");
@@ -509,6 +750,184 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
   return DG_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// reduced-basis preconditioner and initial guess (Sec. 3.2)
+// ------------------------------------------------------------------------------------------
+static int ensure_rb(Solver* S, int cap) {
+  if (cap < 1 || cap > RB_MAX) return fail(DG_EINVAL, "reduced basis size must be in 1..16");
+  if (S->rb_ring && S->rb_cap >= cap) return DG_OK;
+  double** bufs[] = {&S->rb_ring, &S->rb_W, &S->rb_Z, &S->rb_Y};
+  for (double** b : bufs)
+    if (*b) {
+      cudaFree(*b);
+      *b = nullptr;
+    }
+  S->rb_count = S->rb_head = S->rb_r = 0;
+  S->rb_ready = false;
+  cudaError_t err = cudaSuccess;
+  for (double** b : bufs)
+    if (err == cudaSuccess) err = cudaMalloc(b, sizeof(double) * (size_t)cap * S->n);
+  if (err == cudaSuccess && !S->rb_C) err = cudaMalloc(&S->rb_C, sizeof(double) * RB_MAX * RB_MAX);
+  if (err == cudaSuccess && !S->rb_s) err = cudaMalloc(&S->rb_s, sizeof(double) * 2 * RB_MAX);
+  if (err != cudaSuccess) return fail(DG_ENOMEM, std::string("reduced-basis storage: ") + cudaGetErrorString(err));
+  S->rb_cap = cap;
+  return DG_OK;
+}
+
+static void rb_push(Solver* S, const double* du, cudaStream_t s) {
+  cudaMemcpyAsync(S->rb_ring + (long long)S->rb_head * S->n, du, sizeof(double) * S->n, cudaMemcpyDeviceToDevice, s);
+  S->rb_head = (S->rb_head + 1) % S->rb_cap;
+  if (S->rb_count < S->rb_cap) ++S->rb_count;
+}
+
+// rows 0..k-1 of V^T x and |x|^2 into host out[0..k] (one synchronisation)
+static int host_dots(dg_mesh* m, Solver* S, const double* V, int k, const double* x, double* out, cudaStream_t s) {
+  prof_begin(m, s, KK_BLAS);
+  mdot(S->n, k, V, x, S->partial, s);
+  k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev, 0);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_mdot");
+  DG_CUDA_TRY(cudaMemcpyAsync(S->hhost, S->hdev, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s));
+  DG_CUDA_TRY(cudaStreamSynchronize(s));
+  std::memcpy(out, S->hhost, sizeof(double) * (k + 1));
+  return DG_OK;
+}
+
+// in-place inverse of an r x r row-major matrix (Gauss-Jordan, partial pivoting); false if singular
+static bool small_inverse(std::vector<double>& A, int r) {
+  std::vector<int> perm(r);
+  for (int i = 0; i < r; ++i) perm[i] = i;
+  double amax = 0.0;
+  for (double v : A) amax = std::max(amax, std::fabs(v));
+  if (!(amax > 0.0) || !std::isfinite(amax)) return false;
+  for (int k = 0; k < r; ++k) {
+    int p = k;
+    for (int i = k + 1; i < r; ++i)
+      if (std::fabs(A[i * r + k]) > std::fabs(A[p * r + k])) p = i;
+    if (!(std::fabs(A[p * r + k]) > 1e-14 * amax)) return false;
+    if (p != k) {
+      for (int j = 0; j < r; ++j) std::swap(A[k * r + j], A[p * r + j]);
+      std::swap(perm[k], perm[p]);
+    }
+    const double d = 1.0 / A[k * r + k];
+    A[k * r + k] = 1.0;
+    for (int j = 0; j < r; ++j) A[k * r + j] *= d;
+    for (int i = 0; i < r; ++i) {
+      if (i == k) continue;
+      const double f = A[i * r + k];
+      A[i * r + k] = 0.0;
+      for (int j = 0; j < r; ++j) A[i * r + j] -= f * A[k * r + j];
+    }
+  }
+  // columns come out permuted like the rows were: undo
+  std::vector<double> B(A);
+  for (int i = 0; i < r; ++i)
+    for (int k = 0; k < r; ++k) A[i * r + perm[k]] = B[i * r + k];
+  return true;
+}
+
+static int base_solve(dg_mesh* m, Solver* S, int kind, const double* x, double* y, cudaStream_t s);
+
+// orthonormalise the window (newest first) into W; updates within 1e-10 of the span of the kept
+// ones are dropped
+static int rb_orthonormalise(dg_mesh* m, Solver* S, cudaStream_t s) {
+  const long long n = S->n;
+  int r = 0;
+  std::vector<double> d(RB_MAX + 1);
+  for (int q = 0; q < S->rb_count; ++q) {
+    const int slot = ((S->rb_head - 1 - q) % S->rb_cap + S->rb_cap) % S->rb_cap;
+    double* w = S->rb_W + (long long)r * n;
+    DG_CUDA_TRY(cudaMemcpyAsync(w, S->rb_ring + (long long)slot * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    int rc = host_dots(m, S, S->rb_W, r, w, d.data(), s);   // h1 = W^T w and |w|^2
+    if (rc) return rc;
+    const double n0 = d[r];
+    double nf = n0;
+    if (r > 0) {   // h1 is in hdev[0..r-1]
+      prof_begin(m, s, KK_BLAS);
+      update_dot(n, r, S->rb_W, S->hdev, w, S->partial, true, s);
+      k_mdot_finish<<<1, MAXK, 0, s>>>(r - 1, S->partial, S->hdev + MAXK, 0);
+      update_dot(n, r, S->rb_W, S->hdev + MAXK, w, S->partial, false, s);
+      k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev + 2 * MAXK - 1, 0);
+      prof_end(m, s);
+      DG_LAUNCH_CHECK("rb orthonormalise");
+      DG_CUDA_TRY(cudaMemcpyAsync(S->hhost, S->hdev + 2 * MAXK - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+      DG_CUDA_TRY(cudaStreamSynchronize(s));
+      nf = S->hhost[0];
+    } else {
+      S->hhost[0] = n0;
+      DG_CUDA_TRY(cudaMemcpyAsync(S->hdev + 2 * MAXK - 1, S->hhost, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    if (!std::isfinite(n0) || !std::isfinite(nf)) return fail(DG_ENAN, "reduced basis: non-finite Newton update");
+    if (!(n0 > 0.0) || !(nf > 1e-20 * n0)) continue;
+    prof_begin(m, s, KK_BLAS);
+    k_scale_dev<<<grid_for(n), 256, 0, s>>>(n, w, S->hdev + 2 * MAXK - 1, w);
+    prof_end(m, s);
+    DG_LAUNCH_CHECK("k_scale_dev");
+    ++r;
+  }
+  S->rb_r = r;
+  return DG_OK;
+}
+
+// W, Z = J_G W, Y = P0^{-1} Z - W, C = (W^T P0^{-1} Z)^{-1} and Z^T Z at state U
+static int rb_build(dg_mesh* m, Solver* S, int kind, const double* U, double t, double c, int jv_mode, int jv_prec,
+                    cudaStream_t s);
+
+static int rb_apply(dg_mesh* m, Solver* S, const double* x, double* y, cudaStream_t s) {
+  if (!S->rb_ready) return fail(DG_EINVAL, "reduced-basis preconditioner used before it was built");
+  int rc = base_solve(m, S, S->rb_kind, x, y, s);
+  if (rc) return rc;
+  const int r = S->rb_r;
+  if (r == 0) return DG_OK;
+  const long long n = S->n;
+  prof_begin(m, s, KK_PRECOND);
+  mdot(n, r, S->rb_W, y, S->partial, s);
+  k_mdot_finish<<<1, MAXK, 0, s>>>(r - 1, S->partial, S->rb_s, 0);
+  k_small_matvec<<<1, 32, 0, s>>>(r, S->rb_C, S->rb_s, S->rb_s + RB_MAX);
+  k_maxpy<<<grid_for(n), 256, 0, s>>>(n, r, S->rb_Y, n, S->rb_s + RB_MAX, y);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("rb apply");
+  return DG_OK;
+}
+
+// x0 = W a, a = argmin |b - Z a|, and r0 = b - Z a; false (nothing written) when the space is
+// empty or the guess does not reduce |b|
+static int rb_guess(dg_mesh* m, Solver* S, const double* b, double* x0, double* r0, bool* used, cudaStream_t s) {
+  *used = false;
+  const int r = S->rb_r;
+  if (!S->rb_ready || r == 0) return DG_OK;
+  const long long n = S->n;
+  std::vector<double> g(r + 1);
+  int rc = host_dots(m, S, S->rb_Z, r, b, g.data(), s);
+  if (rc) return rc;
+  const double bb = g[r];
+  std::vector<double> Gi(S->rb_gram);
+  if (!small_inverse(Gi, r)) return DG_OK;
+  std::vector<double> a(r, 0.0);
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < r; ++j) a[i] += Gi[i * r + j] * g[j];
+  // |b - Z a|^2 = |b|^2 - 2 a^T g + a^T G a, checked on the device below
+  std::memcpy(S->hhost, a.data(), sizeof(double) * r);
+  DG_CUDA_TRY(cudaMemcpyAsync(S->rb_s, S->hhost, sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  DG_CUDA_TRY(cudaMemcpyAsync(r0, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  prof_begin(m, s, KK_BLAS);
+  k_maxpy<<<grid_for(n), 256, 0, s>>>(n, r, S->rb_Z, n, S->rb_s, r0);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_maxpy");
+  double rr = 0.0;
+  rc = host_dots(m, S, S->rb_Z, 0, r0, &rr, s);
+  if (rc) return rc;
+  if (!std::isfinite(rr) || !(rr < bb)) return DG_OK;
+  std::memcpy(S->hhost, a.data(), sizeof(double) * r);
+  DG_CUDA_TRY(cudaMemcpyAsync(S->rb_s, S->hhost, sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  prof_begin(m, s, KK_BLAS);
+  k_combine<<<grid_for(n), 256, 0, s>>>(n, r, S->rb_W, n, S->rb_s, x0);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_combine");
+  *used = true;
+  return DG_OK;
+}
+
 static int precond_apply(dg_mesh* m, Solver* S, int kind, const double* x, double* y, cudaStream_t s) {
   if (kind == DG_PC_NONE) {
     if (x != y) DG_CUDA_TRY(cudaMemcpyAsync(y, x, sizeof(double) * S->n, cudaMemcpyDeviceToDevice, s));
@@ -529,12 +948,63 @@ static int precond_apply(dg_mesh* m, Solver* S, int kind, const double* x, doubl
     prof_end(m, s);
     return rc;
   }
+  if (kind == DG_PC_RB || kind == DG_PC_RB_BJ) {
+    if (S->rb_ready && S->rb_kind != kind) return fail(DG_EINVAL, "reduced basis was built for the other base");
+    return rb_apply(m, S, x, y, s);
+  }
   return fail(DG_EINVAL, "unknown preconditioner kind");
+}
+
+// base of the reduced-basis preconditioner: M^{-1} (DG_PC_RB) or block-Jacobi (DG_PC_RB_BJ)
+static int base_solve(dg_mesh* m, Solver* S, int kind, const double* x, double* y, cudaStream_t s) {
+  if (kind == DG_PC_RB_BJ) return precond_apply(m, S, DG_PC_BJ, x, y, s);
+  return dg_mass_inverse_apply(m, x, y, s);
+}
+
+static int rb_build(dg_mesh* m, Solver* S, int kind, const double* U, double t, double c, int jv_mode, int jv_prec,
+                    cudaStream_t s) {
+  const long long n = S->n;
+  S->rb_ready = false;
+  S->rb_kind = kind;
+  int rc = rb_orthonormalise(m, S, s);
+  if (rc) return rc;
+  int r = S->rb_r;
+  for (int j = 0; j < r; ++j) {
+    double* Zj = S->rb_Z + (long long)j * n;
+    double* Yj = S->rb_Y + (long long)j * n;
+    rc = stage_matvec(m, S, U, t, c, jv_mode, jv_prec, S->rb_W + (long long)j * n, Zj, s);
+    if (rc) return rc;
+    rc = base_solve(m, S, kind, Zj, Yj, s);
+    if (rc) return rc;
+    prof_begin(m, s, KK_BLAS);
+    k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, Yj, -1.0, S->rb_W + (long long)j * n, 0.0, nullptr, Yj);
+    prof_end(m, s);
+    DG_LAUNCH_CHECK("k_lincomb");
+  }
+  std::vector<double> Cm((size_t)r * r), G((size_t)r * r), d(RB_MAX + 1);
+  for (int j = 0; j < r; ++j) {
+    rc = host_dots(m, S, S->rb_W, r, S->rb_Y + (long long)j * n, d.data(), s);   // W^T Y_j
+    if (rc) return rc;
+    for (int i = 0; i < r; ++i) Cm[i * r + j] = d[i] + (i == j ? 1.0 : 0.0);
+    rc = host_dots(m, S, S->rb_Z, r, S->rb_Z + (long long)j * n, d.data(), s);   // Z^T Z_j
+    if (rc) return rc;
+    for (int i = 0; i < r; ++i) G[i * r + j] = d[i];
+  }
+  if (r > 0 && !small_inverse(Cm, r)) r = 0;   // singular reduced operator: base alone
+  S->rb_r = r;
+  S->rb_gram = G;
+  if (r > 0) {
+    std::memcpy(S->hhost, Cm.data(), sizeof(double) * r * r);
+    DG_CUDA_TRY(cudaMemcpyAsync(S->rb_C, S->hhost, sizeof(double) * r * r, cudaMemcpyHostToDevice, s));
+    DG_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  S->rb_ready = true;
+  return DG_OK;
 }
 
 // (re)build the preconditioner of kind at state U
 static int pc_setup(dg_mesh* m, Solver* S, int kind, const double* U, double t, double c, cudaStream_t s, bool f32) {
-  if (kind == DG_PC_BJ) return bj_setup(m, S, U, t, c, s, f32);
+  if (kind == DG_PC_BJ || kind == DG_PC_RB_BJ) return bj_setup(m, S, U, t, c, s, f32);
   if (kind == DG_PC_MLP) return mlp_setup(m, U, c, s);
   return DG_OK;
 }
@@ -542,8 +1012,9 @@ static int pc_setup(dg_mesh* m, Solver* S, int kind, const double* U, double t, 
 // ------------------------------------------------------------------------------------------
 // GMRES(restart), right preconditioned: solves J_G x = b to ||b - J_G x|| <= tol ||b||
 // ------------------------------------------------------------------------------------------
+// x0_given: x holds an initial guess and the work vector VRES already holds b - J_G x
 static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U, double t, double c,
-                 const double* b, double* x, int* iters, cudaStream_t s) {
+                 const double* b, double* x, int* iters, cudaStream_t s, bool x0_given = false) {
   const long long n = S->n;
   const int R = o.gmres_restart;
   double* V = S->V;
@@ -554,13 +1025,13 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
   int rc = norm2(m, S, b, &bnorm, s);
   if (rc) return rc;
   if (!std::isfinite(bnorm)) return fail(DG_ENAN, "GMRES: non-finite right-hand side");
-  DG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  if (!x0_given || bnorm == 0.0) DG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   if (bnorm == 0.0) return DG_OK;
   std::vector<double> H((size_t)(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
   for (int cycle = 0; cycle < o.max_restarts; ++cycle) {
     // r = b - A x
     if (cycle == 0) {
-      DG_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      if (!x0_given) DG_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     } else {
       rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, x, w, s);
       if (rc) return rc;
@@ -585,13 +1056,12 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
       if (rc) return rc;
       // classical Gram-Schmidt twice; h and the norm stay on the device until one read-back
       prof_begin(m, s, KK_BLAS);
-      k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k + 1, V, n, w, S->partial);
-      k_mdot_finish<<<1, MAXK, 0, s>>>(k + 1, S->partial, S->hdev, 0);
-      k_maxpy<<<grid_for(n), 256, 0, s>>>(n, k + 1, V, n, S->hdev, w);
-      k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k + 1, V, n, w, S->partial);
-      k_mdot_finish<<<1, MAXK, 0, s>>>(k + 1, S->partial, S->hdev + MAXK, 0);
-      k_maxpy<<<grid_for(n), 256, 0, s>>>(n, k + 1, V, n, S->hdev + MAXK, w);
-      k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, 0, V, n, w, S->partial);
+      // h1 = V^T w; w -= V h1 fused with h2 = V^T w; w -= V h2 fused with |w|^2
+      mdot(n, k + 1, V, w, S->partial, s);
+      k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev, 0);
+      update_dot(n, k + 1, V, S->hdev, w, S->partial, true, s);
+      k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev + MAXK, 0);
+      update_dot(n, k + 1, V, S->hdev + MAXK, w, S->partial, false, s);
       k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev + MAXK + k + 1, 0);
       k_scale_dev<<<grid_for(n), 256, 0, s>>>(n, w, S->hdev + MAXK + k + 1, V + (long long)(k + 1) * n);
       prof_end(m, s);
@@ -656,6 +1126,7 @@ extern "C" void dg_solver_opts_default(dg_solver_opts* o) {
   o->newton_rtol = 1e-8;
   o->gmres_rtol = 1e-3;
   o->abs_floor = 1e-14;
+  o->rb_size = 8;
 }
 
 extern "C" int dg_precond_setup(dg_mesh* mesh, int32_t kind, const double* u, double t, double dt_aii,
@@ -676,6 +1147,48 @@ extern "C" int dg_precond_apply(dg_mesh* mesh, int32_t kind, const double* x, do
   return precond_apply(mesh, mesh->solver, kind, x, y, (cudaStream_t)stream);
 }
 
+extern "C" int dg_rb_load(dg_mesh* mesh, const double* w, int32_t r, const double* u, double t, double dt_aii,
+                          int32_t base, void* stream) {
+  if (!mesh || !u || (r > 0 && !w) || r < 0 || r > RB_MAX) return fail(DG_EINVAL, "dg_rb_load: bad argument");
+  if (base != DG_PC_RB && base != DG_PC_RB_BJ) return fail(DG_EINVAL, "dg_rb_load: base must be DG_PC_RB or DG_PC_RB_BJ");
+  Solver* S = nullptr;
+  int rc = solver_get(mesh, mesh->solver ? mesh->solver->restart : 30, &S);
+  if (rc) return rc;
+  rc = ensure_rb(S, std::max(r, std::max(S->rb_cap, 1)));
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  S->rb_count = S->rb_head = 0;
+  for (int j = 0; j < r; ++j) rb_push(S, w + (long long)j * S->n, s);
+  if (base == DG_PC_RB_BJ) {
+    rc = bj_setup(mesh, S, u, t, dt_aii, s);
+    if (rc) return rc;
+  }
+  return rb_build(mesh, S, base, u, t, dt_aii, DG_JV_EXACT, DG_PREC_F64, s);
+}
+
+extern "C" int dg_rb_initial_guess(dg_mesh* mesh, const double* b, double* x0, void* stream) {
+  if (!mesh || !b || !x0) return fail(DG_EINVAL, "dg_rb_initial_guess: null argument");
+  Solver* S = mesh->solver;
+  if (!S || !S->rb_ready) return fail(DG_EINVAL, "dg_rb_initial_guess: no reduced basis was built");
+  cudaStream_t s = (cudaStream_t)stream;
+  bool used = false;
+  int rc = rb_guess(mesh, S, b, x0, S->v(VRES), &used, s);
+  if (rc) return rc;
+  if (!used) DG_CUDA_TRY(cudaMemsetAsync(x0, 0, sizeof(double) * S->n, s));
+  DG_CUDA_TRY(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+extern "C" int dg_rb_reset(dg_mesh* mesh) {
+  if (!mesh) return fail(DG_EINVAL, "dg_rb_reset: null argument");
+  Solver* S = mesh->solver;
+  if (S) {
+    S->rb_count = S->rb_head = S->rb_r = 0;
+    S->rb_ready = false;
+  }
+  return DG_OK;
+}
+
 extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, const dg_solver_opts* opts,
                                 dg_step_stats* stats, void* stream) {
   if (!mesh || !u || !opts) return fail(DG_EINVAL, "dg_implicit_step: null argument");
@@ -686,9 +1199,15 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
   int rc = dirk_tableau(o.stages, A, c);
   if (rc) return rc;
   if (o.max_newton < 1 || o.max_restarts < 1) return fail(DG_EINVAL, "dg_implicit_step: bad limits");
+  if (o.precond < DG_PC_NONE || o.precond > DG_PC_RB_BJ) return fail(DG_EINVAL, "dg_implicit_step: unknown precond");
+  const bool rb = o.precond == DG_PC_RB || o.precond == DG_PC_RB_BJ;
   Solver* S = nullptr;
   rc = solver_get(mesh, o.gmres_restart, &S);
   if (rc) return rc;
+  if (rb) {
+    rc = ensure_rb(S, o.rb_size);
+    if (rc) return rc;
+  }
   dg_step_stats st;
   std::memset(&st, 0, sizeof(st));
   const long long n = S->n;
@@ -761,10 +1280,19 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
       // dU = -J_G^{-1} G
       k_lincomb<<<grid_for(n), 256, 0, s>>>(n, -1.0, G, 0.0, nullptr, 0.0, nullptr, G);
       DG_LAUNCH_CHECK("k_lincomb");
+      bool x0 = false;
+      if (rb) {   // reduced basis of the last Newton updates at the current iterate, and its guess
+        const auto p0 = std::chrono::steady_clock::now();
+        rc = rb_build(mesh, S, o.precond, U, ti, ci, o.jv_mode, o.jv_prec, s);
+        if (!rc) rc = rb_guess(mesh, S, G, dU, S->v(VRES), &x0, s);
+        st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
+        if (rc) return finish(rc);
+      }
       int gits = 0;
-      rc = gmres(mesh, S, o, U, ti, ci, G, dU, &gits, s);
+      rc = gmres(mesh, S, o, U, ti, ci, G, dU, &gits, s, x0);
       st.gmres_iters[i] += gits;
       if (rc) return finish(rc);
+      if (rb) rb_push(S, dU, s);
       k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, U, 1.0, dU, 0.0, nullptr, U);
       DG_LAUNCH_CHECK("k_lincomb");
     }

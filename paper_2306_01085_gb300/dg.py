@@ -40,7 +40,8 @@ class DgSolverOpts(ctypes.Structure):
         ("stages", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
         ("max_newton", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_refresh", ctypes.c_int32),
         ("jv_mode", ctypes.c_int32), ("jv_prec", ctypes.c_int32), ("newton_rtol", ctypes.c_double),
-        ("gmres_rtol", ctypes.c_double), ("abs_floor", ctypes.c_double),
+        ("gmres_rtol", ctypes.c_double), ("abs_floor", ctypes.c_double), ("rb_size", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -52,7 +53,7 @@ class DgStepStats(ctypes.Structure):
     ]
 
 
-PC = {"none": 0, "bj": 1, "mlp": 2}
+PC = {"none": 0, "bj": 1, "mlp": 2, "rb": 3, "rb_bj": 4}
 REFRESH = {"step": 0, "stage": 1, "newton": 2}
 
 _lib = None
@@ -107,6 +108,10 @@ def lib():
     L.dg_precond_apply.argtypes = [vp, i32, dp, dp, vp]
     L.dg_block_assemble.argtypes = [vp, dp, d, d, dp, vp]
     L.dg_eval_precision.argtypes = [vp, i32, dp, dp, d, dp, dp, vp]
+    L.dg_mass_inverse_apply.argtypes = [vp, dp, dp, vp]
+    L.dg_rb_load.argtypes = [vp, dp, i32, dp, d, d, i32, vp]
+    L.dg_rb_initial_guess.argtypes = [vp, dp, dp, vp]
+    L.dg_rb_reset.argtypes = [vp]
     _lib = L
     return L
 
@@ -214,6 +219,12 @@ class Mesh:
     def mass(self, v, out=None):
         mv = out if out is not None else self.empty()
         _check(lib().dg_mass_apply(self._h, _ptr(v, self.u_shape, "v"), _ptr(mv, self.u_shape, "mv"), _stream()))
+        return mv
+
+    def mass_inverse(self, v, out=None):
+        mv = out if out is not None else self.empty()
+        _check(lib().dg_mass_inverse_apply(self._h, _ptr(v, self.u_shape, "v"), _ptr(mv, self.u_shape, "mv"),
+                                           _stream()))
         return mv
 
     # -- tracing ---------------------------------------------------------------------------
@@ -416,3 +427,30 @@ def _mesh_eval_precision(self, mode, u, v=None, t=0.0, r=None, jv=None):
 
 
 Mesh.eval_precision = _mesh_eval_precision
+
+
+def _mesh_rb_load(self, w, u, t, dt_aii, base="rb"):
+    """Replace the reduced basis by the rows of w ([r][n_elem][5][n_p] device FP64) and build the
+    RB preconditioner at (u, t, dt_aii) over base "rb" (mass) or "rb_bj" (block-Jacobi)."""
+    import torch
+    r = int(w.shape[0]) if w is not None else 0
+    if r and not (w.is_cuda and w.dtype == torch.float64 and w.is_contiguous()
+                  and tuple(w.shape[1:]) == tuple(self.u_shape)):
+        raise DgError("w must be a contiguous float64 CUDA tensor [r][n_elem][5][n_p]")
+    _check(lib().dg_rb_load(self._h, ctypes.c_void_p(w.data_ptr()) if r else None, r, _ptr(u, self.u_shape, "u"),
+                            float(t), float(dt_aii), PC[base], _stream()))
+
+
+def _mesh_rb_initial_guess(self, b, out=None):
+    x0 = out if out is not None else self.empty()
+    _check(lib().dg_rb_initial_guess(self._h, _ptr(b, self.u_shape, "b"), _ptr(x0, self.u_shape, "x0"), _stream()))
+    return x0
+
+
+def _mesh_rb_reset(self):
+    _check(lib().dg_rb_reset(self._h))
+
+
+Mesh.rb_load = _mesh_rb_load
+Mesh.rb_initial_guess = _mesh_rb_initial_guess
+Mesh.rb_reset = _mesh_rb_reset
