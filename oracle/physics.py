@@ -22,6 +22,8 @@ import math
 
 import numpy as np
 
+from . import euvac as _euvac
+
 
 class Coeffs:
     """Nondimensional numbers of one workload (Eq. nondimensional)."""
@@ -48,6 +50,9 @@ class Coeffs:
         self.euv_r_peak = desc.euv_r_peak
         self.euv_width = desc.euv_width
         self.euv_omega_t = desc.euv_omega_t
+        for k in ("euv_day", "euv_f107", "euv_f107a", "euv_eff", "euv_dsun", "ref_T0", "ref_rho0", "ref_m",
+                  "ref_g0"):
+            setattr(self, k, getattr(desc, k))
 
 
 def _transport(T, C):
@@ -121,7 +126,7 @@ def euv_heating(x, t, C):
     rotating frame at equinox (declination 0), cf. the zenith-angle formula of Sec. 2.2.
     """
     r = np.sqrt(x[0] ** 2 + x[1] ** 2 + x[2] ** 2)
-    if not C.euv:
+    if C.euv != 1:
         return np.zeros_like(r)
     sx, sy = math.cos(C.euv_omega_t * t), -math.sin(C.euv_omega_t * t)
     cchi = np.clip((x[0] * sx + x[1] * sy) / r, -1.0, 1.0)
@@ -142,7 +147,8 @@ def source(u, q, x, t, C):
                  + 0.5 * C.c_mu * mu * isr * eps_grad)
     gT_grad = gT[0] * q[0, 0] + gT[1] * q[1, 0] + gT[2] * q[2, 0]
     diss = sum(eps[m, d] * gv[m, d] for m in range(3) for d in range(3))
-    s.append(euv_heating(x, t, C) * isr / C.cv
+    heat = _euvac.heating(u, x, t, C) if C.euv == 2 else euv_heating(x, t, C)
+    s.append(heat * isr / C.cv
              + (1.5 - C.gamma) * u[4] * div
              + 0.5 * C.c_kappa * kappa * isr / C.cv * gT_grad
              + C.c_diss * mu * isr / C.cv * diss)

@@ -21,6 +21,7 @@ import numpy as np
 # ----------------------------------------------------------------------------------------------
 # SI constants of the thermosphere workloads (Sec. 2; reference values at the lower boundary, Sec. 2.4)
 # ----------------------------------------------------------------------------------------------
+EUV_GAUSS, EUV_EUVAC = 1, 2  # heating models: sub-solar Gaussian; EUVAC flux with Chapman depths
 K_B = 1.380649e-23          # Boltzmann constant [J/K]
 AMU = 1.66053906660e-27     # atomic mass unit [kg]
 R_EARTH = 6371.0e3          # Earth radius [m]
@@ -78,6 +79,16 @@ class MeshDesc:
     euv_r_peak: float = 0.0     # radius of the heating peak (nondimensional)
     euv_width: float = 0.0      # vertical half width at half maximum (nondimensional)
     euv_omega_t: float = 0.0    # rotation angle of the sub-solar point per unit nondimensional time
+    # EUVAC heating (euv = EUV_EUVAC, Sec. 2.2): solar and reference data
+    euv_day: float = 80.0       # day of the year N_d (1 = January 1st)
+    euv_f107: float = 150.0     # daily F10.7 index
+    euv_f107a: float = 150.0    # its 81-day mean
+    euv_eff: float = 0.25       # heating efficiency epsilon
+    euv_dsun: float = 1.0       # Sun distance [astronomical units]
+    ref_T0: float = 0.0         # reference temperature [K]
+    ref_rho0: float = 0.0       # reference density [kg/m^3]
+    ref_m: float = 0.0          # reference molecular mass [kg]
+    ref_g0: float = 0.0         # reference gravity at the inner radius [m/s^2]
 
     def as_dict(self):
         return asdict(self)
@@ -150,7 +161,7 @@ def box_desc(p=2, n=4, re=100.0, pr=0.7, bc_lo=BC_PERIODIC, bc_hi=BC_PERIODIC, g
 
 
 def shell_desc(n=16, nr=8, p=4, euv=False, rotation=True, h_first_km=2.5, ref: Reference | None = None,
-               bc_lo=BC_WALL, bc_hi=BC_OUTFLOW) -> MeshDesc:
+               bc_lo=BC_WALL, bc_hi=BC_OUTFLOW, euvac=False, day=80.0, f107=150.0, f107a=150.0) -> MeshDesc:
     """Cubed-sphere shell 100-600 km (Sec. 3.3) with the nondimensional numbers of Sec. 2.4."""
     ref = ref or shell_reference()
     H0 = ref.H0
@@ -169,6 +180,11 @@ def shell_desc(n=16, nr=8, p=4, euv=False, rotation=True, h_first_km=2.5, ref: R
         d.euv_r_peak = (R_EARTH + 300.0e3) / H0
         d.euv_width = 50.0e3 / H0
         d.euv_omega_t = OMEGA_EARTH * ref.t0
+    if euvac:
+        d.euv = EUV_EUVAC
+        d.euv_omega_t = OMEGA_EARTH * ref.t0
+        d.euv_day, d.euv_f107, d.euv_f107a = day, f107, f107a
+    d.ref_T0, d.ref_rho0, d.ref_m, d.ref_g0 = ref.T0, ref.rho0, ref.m_O, ref.g0
     return d
 
 
