@@ -281,13 +281,15 @@ def main_ours(args):
     dom_name, (dom_ms, dom_cnt) = dom
     per_launch_ms = dom_ms / dom_cnt
     key = (dom_name, desc.p + 1)
-    flops = FP64_FLOPS_PER_ELEMENT.get(key, float("nan")) * mesh.n_elem
-    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+    fpe = FP64_FLOPS_PER_ELEMENT.get(key)
+    flops = fpe * mesh.n_elem if fpe else None
+    achieved = flops / (per_launch_ms * 1e-3) / 1e12 if flops else None
     probe = DG.probe_fp64()
     fresh = residual_kernel_digest() == CAPTURE_DIGEST
     traffic = DRAM_BYTES_PER_LAUNCH.get(key) if (args.config == CONFIG_NAME and fresh) else None
-    roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+    roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4) if achieved else None,
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4) if achieved else None, "traffic": traffic,
                 "peak_kind": "FP64 from unit counts x max SM clock (2 DFMA/SM/cycle, 152 SMs, 2.07 GHz)",
                 "flops_kind": FLOPS_KIND.get(dom_name),
                 "peak_probe": round(probe, 4), "launch_ms": round(per_launch_ms, 4), "fp64_flops_per_launch": flops,

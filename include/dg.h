@@ -64,7 +64,7 @@ typedef struct dg_mesh_desc {
     double lambda0;        /* sigma_c = lambda0 I (global Lax-Friedrichs, Eq. LDG2) */
     double t_wall;         /* wall temperature T* */
     int32_t gravity_kind;  /* 0: constant g* = gvec; 1: g* = -(g_r0/|r|)^2 r/|r| */
-    int32_t euv;           /* 1: Gaussian sub-solar heating source */
+    int32_t euv;           /* DG_EUV_GAUSS: sub-solar Gaussian heating; DG_EUV_EUVAC: EUVAC / Chapman */
     double gvec[3];
     double g_r0;
     double omega[3];       /* rotation vector omega* */
@@ -74,7 +74,34 @@ typedef struct dg_mesh_desc {
     double euv_r_peak;     /* radius of the peak */
     double euv_width;      /* vertical half width at half maximum */
     double euv_omega_t;    /* sub-solar rotation angle per unit nondimensional time */
+    /* DG_EUV_EUVAC (Sec. 2.2): q_euv = eps n sum_j phi_j I0_j exp(-tau_j) h c/lambda_j for the single
+     * constituent (atomic oxygen) with the flux, cross sections and Chapman optical depths described
+     * at DG_EUV_EUVAC; q* = q H0 / (rho0 c_v0 T0 a0) enters the energy source as q* e^{-varrho/2}/c_v */
+    double euv_day;        /* day of the year N_d (solar declination) */
+    double euv_f107;       /* daily F10.7 index */
+    double euv_f107a;      /* its 81-day mean */
+    double euv_eff;        /* heating efficiency epsilon */
+    double euv_dsun;       /* Sun distance [astronomical units] */
+    double ref_T0;         /* reference temperature [K] */
+    double ref_rho0;       /* reference density [kg/m^3] */
+    double ref_m;          /* reference molecular mass [kg] (m = ref_m * mass) */
+    double ref_g0;         /* gravity at the radius g_r0 [m/s^2] */
 } dg_mesh_desc;
+
+/*
+ * Heating models (dg_mesh_desc.euv):
+ * DG_EUV_GAUSS: Q* = euv_amp exp(-chi^2/(2 sigma^2)) exp(-ln 2 ((|r| - r_peak)/w)^2), cos chi = r.s/|r|,
+ *   s = (cos wt, -sin wt, 0).
+ * DG_EUV_EUVAC: I0_j = F_j max{0.8, 1 + A_j ((F10.7 + F10.7_81)/2 - 80)} / d^2 over the 37 bands of
+ *   the paper's appendix table (band centres or lines for lambda_j); tau_j = n phi_j H Ch with
+ *   H = k_B T/(m g), r~ = |r|/H, y = sqrt(r~/2)|cos chi| and the Smith & Smith Chapman factor
+ *   Ch = sqrt(pi r~/2) erfcx(y) (cos chi > 0), sqrt(pi r~/2)(2 exp(r~(1 - sin chi)) - erfcx(y))
+ *   (cos chi <= 0 and sin chi > R0/|r|), no heating in the Earth's shadow; the Sun direction in the
+ *   rotating frame is s = (-cos(delta) cos(wt), cos(delta) sin(wt), sin(delta)) with the declination
+ *   delta = asin(sin(-23.44 deg) cos(2 pi/365.24 (N_d + 9) + 2 (0.0167) sin(2 pi/365.24 (N_d - 3)))).
+ */
+#define DG_EUV_GAUSS 1
+#define DG_EUV_EUVAC 2
 
 typedef struct dg_mesh dg_mesh;
 
@@ -135,8 +162,8 @@ int dg_jvp(dg_mesh* mesh, const double* u, const double* v, double t, int32_t mo
 /*
  * FP32 variants of dg_residual (q from u) and of the exact dg_jvp: the same discrete operators
  * with every intermediate (Gauss values, traces, gradient, fluxes, geometry) stored and computed in
- * FP32, except exp(varrho/2) = sqrt(rho), which is evaluated in FP64 and rounded. Inputs and
- * outputs are FP64 as above. The first call allocates the FP32 workspace and FP32 copies of the
+ * FP32, including exp(varrho/2) = sqrt(rho) (varrho is rounded to FP32 on load, which already bounds
+ * its relative error near 7e-7 at the top of the shells). Inputs and outputs are FP64 as above. The first call allocates the FP32 workspace and FP32 copies of the
  * geometry (synchronises the device once). Used as the inner Jv of the mixed-precision GMRES.
  */
 int dg_residual_f32(dg_mesh* mesh, const double* u, double t, double* r, void* stream);
@@ -151,7 +178,7 @@ int dg_jvp_f32(dg_mesh* mesh, const double* u, const double* v, double t, double
  *   DG_CM_BF16X3 each operand split into bf16 hi + lo, three products (hi hi + hi lo + lo hi)
  *   DG_CM_FP16X3 the same with binary16 parts
  * The arithmetic of each contraction is that of a tensor-core MMA with FP32 accumulation; the
- * pointwise fluxes stay FP32 and exp(varrho/2) FP64. Computes r (v == NULL) or the fused r and exact
+ * pointwise fluxes stay FP32. Computes r (v == NULL) or the fused r and exact
  * J v (r may then be NULL). FP64 inputs and outputs.
  */
 #define DG_CM_FP32   0

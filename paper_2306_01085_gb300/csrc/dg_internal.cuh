@@ -53,6 +53,10 @@ struct Phys {
   double cor;                     // 2 Fr / sqrt(gamma)
   int euv;
   double euv_amp, euv_inv2s2, euv_r_peak, euv_inv_w, euv_omega_t;
+  // EUVAC: Q* = (e^varrho/m*) sum_j b_j exp(-c_j e^varrho H* Ch / m*), H* = T* r*^2/(m* g_r0^2)
+  int n_euvac;
+  double euvac_b[40], euvac_c[40];
+  double sun_cd, sun_sd, g_r0, inv_m;   // cos and sin of the declination, inner radius, 1/m*
 };
 
 // --------------------------------------------------------------------------------------------
@@ -155,7 +159,7 @@ inline void prof_end(dg_mesh* m, cudaStream_t s) {
 template <int N>
 struct Driver {
   static int geometry(dg_mesh* m, cudaStream_t s);
-  // f32: FP32 data and arithmetic (exp(log rho) in FP64); inputs and outputs stay FP64
+  // f32: FP32 data and arithmetic; inputs and outputs stay FP64
   static int gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32 = false);
   static int residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
                       bool tangent, cudaStream_t s, bool f32 = false, double stage_c = 0.0);
@@ -215,16 +219,27 @@ template <typename T> __device__ inline DualT<T> s_exp(DualT<T> x) {
   const T e = s_exp(x.v);
   return {e, e * x.d};
 }
+__device__ inline double s_erfcx(double x) { return erfcx(x); }
+__device__ inline float s_erfcx(float x) { return erfcxf(x); }
+// d/dy erfcx(y) = 2 y erfcx(y) - 2/sqrt(pi)
+template <typename T> __device__ inline DualT<T> s_erfcx(DualT<T> x) {
+  const T e = s_erfcx(x.v);
+  return {e, (T(2) * x.v * e - T(1.1283791670955126)) * x.d};
+}
+template <typename T> __device__ inline T s_inv(T x) { return T(1) / x; }
+template <typename T> __device__ inline DualT<T> s_inv(DualT<T> x) {
+  const T r = T(1) / x.v;
+  return {r, -x.d * r * r};
+}
+__device__ inline double s_sqrt(double x) { return sqrt(x); }
+__device__ inline float s_sqrt(float x) { return sqrtf(x); }
+template <typename T> __device__ inline DualT<T> s_sqrt(DualT<T> x) {
+  const T r = s_sqrt(x.v);
+  return {r, x.d / (T(2) * r)};
+}
 __device__ inline double s_log(double x) { return log(x); }
 __device__ inline float s_log(float x) { return logf(x); }
 template <typename T> __device__ inline DualT<T> s_log(DualT<T> x) { return {s_log(x.v), x.d / x.v}; }
-// exponential evaluated in FP64 whatever the working precision (exp(log rho) stays FP64)
-__device__ inline double s_exp64(double x) { return exp(x); }
-__device__ inline float s_exp64(float x) { return (float)exp((double)x); }
-template <typename T> __device__ inline DualT<T> s_exp64(DualT<T> x) {
-  const T e = s_exp64(x.v);
-  return {e, e * x.d};
-}
 template <typename S> __device__ inline S s_zero() { return S{}; }
 template <typename S> __device__ inline S s_const(typename RealOf<S>::type c);
 template <> __device__ inline double s_const<double>(double c) { return c; }
@@ -240,6 +255,9 @@ struct PhysT {
   R cor;
   int euv;
   R euv_amp, euv_inv2s2, euv_r_peak, euv_inv_w, euv_omega_t;
+  int n_euvac;
+  R euvac_b[40], euvac_c[40];
+  R sun_cd, sun_sd, g_r0, inv_m;
 };
 template <typename R>
 inline PhysT<R> phys_as(const Phys& P) {
@@ -249,6 +267,12 @@ inline PhysT<R> phys_as(const Phys& P) {
   for (int k = 0; k < 3; ++k) q.omega[k] = (R)P.omega[k];
   q.cor = (R)P.cor; q.euv = P.euv; q.euv_amp = (R)P.euv_amp; q.euv_inv2s2 = (R)P.euv_inv2s2;
   q.euv_r_peak = (R)P.euv_r_peak; q.euv_inv_w = (R)P.euv_inv_w; q.euv_omega_t = (R)P.euv_omega_t;
+  q.n_euvac = P.n_euvac;
+  for (int j = 0; j < 40; ++j) {
+    q.euvac_b[j] = (R)P.euvac_b[j];
+    q.euvac_c[j] = (R)P.euvac_c[j];
+  }
+  q.sun_cd = (R)P.sun_cd; q.sun_sd = (R)P.sun_sd; q.g_r0 = (R)P.g_r0; q.inv_m = (R)P.inv_m;
   return q;
 }
 
@@ -263,7 +287,7 @@ struct Prim {
 
 template <typename S, typename R = typename RealOf<S>::type>
 __device__ inline void primitives(const PhysT<R>& P, const S u[5], const S q[3][5], Prim<S>& w) {
-  w.isr = s_exp64(R(-0.5) * u[0]);
+  w.isr = s_exp(R(-0.5) * u[0]);
   for (int m = 0; m < 3; ++m) w.v[m] = u[1 + m] * w.isr;
   w.T = u[4] * w.isr;
   for (int m = 0; m < 3; ++m)
@@ -280,7 +304,7 @@ __device__ inline void primitives(const PhysT<R>& P, const S u[5], const S q[3][
 template <typename S, typename R = typename RealOf<S>::type>
 __device__ inline void flux_dot_n(const PhysT<R>& P, const S u[5], const S q[3][5], const R n[3], bool viscous,
                                   S out[5]) {
-  S isr = s_exp64(R(-0.5) * u[0]);
+  S isr = s_exp(R(-0.5) * u[0]);
   S v[3] = {u[1] * isr, u[2] * isr, u[3] * isr};
   S vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
   out[0] = u[0] * vn;
@@ -300,7 +324,7 @@ __device__ inline void flux_dot_n(const PhysT<R>& P, const S u[5], const S q[3][
 // stabilisation diagonal sigma(u_hat) = lambda0 + sigma_d (Eq. LDG2)
 template <typename S, typename R = typename RealOf<S>::type>
 __device__ inline void sigma_diag(const PhysT<R>& P, const S uh[5], S sg[5]) {
-  S isr = s_exp64(R(-0.5) * uh[0]);
+  S isr = s_exp(R(-0.5) * uh[0]);
   S T = uh[4] * isr;
   S mu = (P.visc_exp != R(0)) ? s_exp(P.visc_exp * s_log(T)) : s_const<S>(R(1));
   S sm = P.lam + (P.c_mu * mu) * isr;
@@ -317,7 +341,7 @@ __device__ inline void wall_trace(const PhysT<R>& P, const S u[5], S ub[5]) {
   ub[1] = s_zero<S>();
   ub[2] = s_zero<S>();
   ub[3] = s_zero<S>();
-  ub[4] = s_exp64(R(0.5) * u[0]) * P.t_wall;
+  ub[4] = s_exp(R(0.5) * u[0]) * P.t_wall;
 }
 
 }  // namespace dg

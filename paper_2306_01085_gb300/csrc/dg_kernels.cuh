@@ -286,7 +286,7 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
         R* xo = qx + (e * 6 + phi) * 15 * NF + f;
         for (int k = 0; k < 15; ++k) xo[k * NF] = R(0);
       }
-      const R sr = s_exp64(R(0.5) * own[0]);
+      const R sr = s_exp(R(0.5) * own[0]);
       dst[0] = own[0];
       dst[NF] = R(0);
       dst[2 * NF] = R(0);
@@ -518,7 +518,7 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
 #pragma unroll
     for (int c = 0; c < 5; ++c) Fref[a][c] = G[a * 3 + 0] * F[c][0] + G[a * 3 + 1] * F[c][1] + G[a * 3 + 2] * F[c][2];
   // source terms
-  const S sr = s_exp64(R(0.5) * u[0]);
+  const S sr = s_exp(R(0.5) * u[0]);
   const S wxv[3] = {P.omega[1] * w.v[2] - P.omega[2] * w.v[1], P.omega[2] * w.v[0] - P.omega[0] * w.v[2],
                     P.omega[0] * w.v[1] - P.omega[1] * w.v[0]};
   src[0] = (u[0] - R(1)) * w.div;
@@ -535,7 +535,7 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
 #pragma unroll
     for (int d = 0; d < 3; ++d) diss = diss + w.eps[m][d] * w.gv[m][d];
   S s4 = (R(1.5) - P.gamma) * (u[4] * w.div) + R(0.5) * (ck * tg) + ((P.c_d / P.cv) * w.mu) * (w.isr * diss);
-  if (P.euv) {
+  if (P.euv == DG_EUV_GAUSS) {
     const R r = sqrt(xg[0] * xg[0] + xg[1] * xg[1] + xg[2] * xg[2]);
     const R sx = cos(P.euv_omega_t * t), sy = -sin(P.euv_omega_t * t);
     R cchi = (xg[0] * sx + xg[1] * sy) / r;
@@ -544,6 +544,28 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
     const R dz = (r - P.euv_r_peak) * P.euv_inv_w;
     const R Qh = P.euv_amp * s_exp(-chi * chi * P.euv_inv2s2) * s_exp(R(-0.6931471805599453) * dz * dz);
     s4 = s4 + (Qh / P.cv) * w.isr;
+  } else if (P.euv == DG_EUV_EUVAC) {
+    // EUVAC photoabsorption with Smith & Smith Chapman depths (Sec. 2.2)
+    const R r = sqrt(xg[0] * xg[0] + xg[1] * xg[1] + xg[2] * xg[2]);
+    const R wt = P.euv_omega_t * t;
+    R cchi = (xg[0] * (-P.sun_cd * cos(wt)) + xg[1] * (P.sun_cd * sin(wt)) + xg[2] * P.sun_sd) / r;
+    cchi = fmin(R(1), fmax(R(-1), cchi));
+    const R schi = sqrt(fmax(R(0), R(1) - cchi * cchi));
+    if (cchi > R(0) || schi * r > P.g_r0) {          // not in the Earth's shadow
+      const S er = sr * sr;                             // e^varrho
+      const S Hs = w.T * (r * r * P.inv_m / (P.g_r0 * P.g_r0));   // H* = T* r*^2 / (m* g_r0^2)
+      const S rt = r * s_inv(Hs);                       // r~ = |r| / H
+      const S ex = s_erfcx(s_sqrt(R(0.5) * rt) * fabs(cchi));
+      const S base = s_sqrt(R(1.5707963267948966) * rt);
+      S ch;
+      if (cchi > R(0)) ch = base * ex;
+      else ch = base * (R(2) * s_exp(rt * (R(1) - schi)) - ex);
+      const S k = er * Hs * ch * P.inv_m;              // tau_j = c_j k
+      S qs = s_zero<S>();
+#pragma unroll 1
+      for (int j = 0; j < P.n_euvac; ++j) qs = qs + P.euvac_b[j] * s_exp(-P.euvac_c[j] * k);
+      s4 = s4 + (er * qs) * (P.inv_m / P.cv) * w.isr;
+    }
   }
   src[4] = s4;
 #pragma unroll

@@ -7,6 +7,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "dg_euvac.h"
 #include "dg_internal.cuh"
 #include "dg_map.cuh"
 
@@ -47,6 +48,41 @@ static int drv_mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s)
 // ------------------------------------------------------------------------------------------
 // radial layers with geometric growth from the first-layer height (Sec. 3.3)
 // ------------------------------------------------------------------------------------------
+// Per-band coefficients of the EUVAC heating in the nondimensional variables (DG_EUV_EUVAC in
+// dg.h): with n = rho0 e^varrho / (m0 m*) and H = H0 H*, q* = q H0/(rho0 c_v0 T0 a0) =
+// (e^varrho/m*) sum_j b_j exp(-tau_j), tau_j = c_j e^varrho H* Ch / m*, where
+// b_j = eps phi_j I0_j (h c/lambda_j) H0 / (m0 c_v0 T0 a0) and c_j = rho0 phi_j H0 / m0.
+static bool euvac_coefficients(const dg_mesh_desc& d, Phys& P) {
+  if (!(d.ref_T0 > 0 && d.ref_rho0 > 0 && d.ref_m > 0 && d.ref_g0 > 0 && d.euv_dsun > 0 && d.g_r0 > 0 &&
+        d.mass > 0 && d.gamma > 1))
+    return false;
+  const double kB = 1.380649e-23, h = 6.62607015e-34, c = 299792458.0;
+  const double H0 = kB * d.ref_T0 / (d.ref_m * d.ref_g0);
+  const double a0 = std::sqrt(d.gamma * kB * d.ref_T0 / d.ref_m);
+  const double cv0 = kB / ((d.gamma - 1.0) * d.ref_m);
+  const double fbar = 0.5 * (d.euv_f107 + d.euv_f107a);
+  int n = 0;
+  for (int j = 0; j < kEuvacRows && n < 40; ++j) {
+    const EuvacRow& row = kEuvac[j];
+    if (row.phi_o == 0.0) continue;
+    const double lambda = 0.5 * (row.lo + row.hi) * 1e-10;
+    const double I0 = row.flux * 1e13 * std::max(0.8, 1.0 + row.a * (fbar - 80.0)) / (d.euv_dsun * d.euv_dsun);
+    const double phi = row.phi_o * 1e-22;
+    P.euvac_b[n] = d.euv_eff * phi * I0 * (h * c / lambda) * H0 / (d.ref_m * cv0 * d.ref_T0 * a0);
+    P.euvac_c[n] = d.ref_rho0 * phi * H0 / d.ref_m;
+    ++n;
+  }
+  P.n_euvac = n;
+  const double w = 2.0 * M_PI / 365.24;
+  const double delta = std::asin(std::sin(-23.44 * M_PI / 180.0) *
+                                 std::cos(w * (d.euv_day + 9.0) + 2.0 * 0.0167 * std::sin(w * (d.euv_day - 3.0))));
+  P.sun_cd = std::cos(delta);
+  P.sun_sd = std::sin(delta);
+  P.g_r0 = d.g_r0;
+  P.inv_m = 1.0 / d.mass;
+  return true;
+}
+
 static std::vector<double> radial_layers(double r_in, double r_out, int nz, double h1) {
   std::vector<double> r(nz + 1);
   const double total = r_out - r_in;
@@ -387,10 +423,15 @@ extern "C" int dg_mesh_create(const dg_mesh_desc* desc, const double* nodes, dg_
   P.cor = 2.0 * d.froude / std::sqrt(d.gamma);
   P.euv = d.euv;
   P.euv_amp = d.euv_amp;
-  P.euv_inv2s2 = d.euv ? 1.0 / (2.0 * d.euv_sigma * d.euv_sigma) : 0.0;
+  P.euv_inv2s2 = d.euv == DG_EUV_GAUSS ? 1.0 / (2.0 * d.euv_sigma * d.euv_sigma) : 0.0;
   P.euv_r_peak = d.euv_r_peak;
-  P.euv_inv_w = d.euv ? 1.0 / d.euv_width : 0.0;
+  P.euv_inv_w = d.euv == DG_EUV_GAUSS ? 1.0 / d.euv_width : 0.0;
   P.euv_omega_t = d.euv_omega_t;
+  P.n_euvac = 0;
+  if (d.euv == DG_EUV_EUVAC && !euvac_coefficients(d, P)) {
+    delete m;
+    return fail(DG_EINVAL, "dg_mesh_create: EUVAC heating needs positive reference values, g_r0 and Sun distance");
+  }
 
   std::vector<double> layers = (d.kind == DG_KIND_SHELL) ? radial_layers(d.r_inner, d.r_outer, d.nz, d.h_first)
                                                          : std::vector<double>(2, 0.0);

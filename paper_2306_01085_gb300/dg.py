@@ -32,6 +32,9 @@ class DgMeshDesc(ctypes.Structure):
         ("gvec", ctypes.c_double * 3), ("g_r0", ctypes.c_double), ("omega", ctypes.c_double * 3),
         ("froude", ctypes.c_double), ("euv_amp", ctypes.c_double), ("euv_sigma", ctypes.c_double),
         ("euv_r_peak", ctypes.c_double), ("euv_width", ctypes.c_double), ("euv_omega_t", ctypes.c_double),
+        ("euv_day", ctypes.c_double), ("euv_f107", ctypes.c_double), ("euv_f107a", ctypes.c_double),
+        ("euv_eff", ctypes.c_double), ("euv_dsun", ctypes.c_double), ("ref_T0", ctypes.c_double),
+        ("ref_rho0", ctypes.c_double), ("ref_m", ctypes.c_double), ("ref_g0", ctypes.c_double),
     ]
 
 
@@ -325,7 +328,7 @@ Mesh.block_assemble = _mesh_block_assemble
 
 
 def _mesh_residual_f32(self, u, t=0.0, out=None):
-    """FP32 residual (FP64 in and out; exp(log rho) in FP64)."""
+    """FP32 residual (FP64 in and out)."""
     r = out if out is not None else self.empty()
     _check(lib().dg_residual_f32(self._h, _ptr(u, self.u_shape, "u"), float(t), _ptr(r, self.u_shape, "r"), _stream()))
     return r

@@ -194,6 +194,8 @@ CONFIGS = {
     "shell16x8_p4": (lambda: shell_desc(n=16, nr=8, p=4), "cubed-sphere shell 6x16x16x8, p=4"),
     "shell32x16_p2_euv": (lambda: shell_desc(n=32, nr=16, p=2, euv=True),
                           "cubed-sphere shell 6x32x32x16, p=2, EUV"),
+    "shell32x16_p2_euvac": (lambda: shell_desc(n=32, nr=16, p=2, euvac=True, day=172.0),
+                            "cubed-sphere shell 6x32x32x16, p=2, EUVAC heating with Chapman depths, June solstice"),
     "shell48x16_p3_euv": (lambda: shell_desc(n=48, nr=16, p=3, euv=True),
                           "cubed-sphere shell 6x48x48x16, p=3, EUV"),
 }

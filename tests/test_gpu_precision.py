@@ -1,6 +1,6 @@
 """Reduced-precision variants against the FP64 oracle, and the mixed-precision implicit step.
 
-FP32 storage and arithmetic (exp(log rho) in FP64): the error of r and J v is reported per
+FP32 storage and arithmetic: the error of r and J v is reported per
 variable as max|x - x_ref| / max|x_ref| and held to 1e-4 (about 1700 eps_32). Two conditioning
 factors multiply eps_32 = 2^-24: the cancellation between the volume, source and face terms of
 the residual (printed as kappa; up to ~220 where pressure balances gravity), and the rounding of
@@ -76,7 +76,9 @@ def test_fp32_residual_and_jv_errors(torch_cuda, case):
     e_r, e_j = _per_var(r32, r_ref), _per_var(jv32, jv_ref)
     e_r2 = _per_var(r2.cpu().numpy(), r_ref)
     print(f"\n{case}: FP32 residual rel. error per variable {e_r}\n{case}: FP32 Jv rel. error per variable {e_j}")
-    assert np.all(e_r2 == e_r) or np.allclose(e_r2, e_r, rtol=1e-3)
+    # the residual of the fused tangent pass is an FP32 evaluation of the same quantity, rounded
+    # differently: as accurate as the plain FP32 residual
+    assert np.all(e_r2 <= 1.5 * e_r + 1e-9), (e_r2, e_r)
     kappa = _cancellation(om, u, 0.1)
     print(f"{case}: cancellation factor per variable {kappa}")
     assert np.all(e_r <= 1e-4), (e_r, kappa)
@@ -109,7 +111,8 @@ def test_contraction_precision_modes(torch_cuda, case):
     """Basis contractions with bfloat16 / binary16 operands and FP32 accumulation (the arithmetic
     of a tensor-core MMA), with and without hi + lo splits, against the FP64 oracle. Reported per
     variable; held to what the arithmetic fixes: the FP32 mode is the FP32 variant bit for bit,
-    one-term bfloat16 is at least as wrong as FP32, and the three-product split recovers most of
+    one-term bfloat16 is at least as wrong as FP32, the fused pass's residual is as accurate as
+    the plain one, and the three-product split recovers most of
     the lost digits (its operands carry 16 bits, so its error is at most 2^-7 of the one-term
     error plus the FP32 floor)."""
     torch = torch_cuda
@@ -134,9 +137,10 @@ def test_contraction_precision_modes(torch_cuda, case):
         r, r2, jv = r.cpu().numpy(), r2.cpu().numpy(), jv.cpu().numpy()
         if mode == "fp32":
             assert np.array_equal(r, r32)
-        assert np.array_equal(r, r2) or mode != "fp32"
         with np.errstate(invalid="ignore"):
             err[mode] = (_per_var(r, r_ref), _per_var(jv, jv_ref))
+            if mode == "fp32":   # the fused pass's residual: same accuracy, its own rounding
+                assert np.all(_per_var(r2, r_ref) <= 1.5 * err[mode][0] + 1e-9)
         print(f"\n{case} {mode:7s} r {err[mode][0]}\n{case} {mode:7s} Jv {err[mode][1]}")
     m.close()
     for k in (0, 1):
