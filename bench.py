@@ -57,6 +57,8 @@ def parse():
                     help="time the implicit DIRK step variants instead (configs shell32x16_p2_euv, shell48x16_p3_euv)")
     ap.add_argument("--variants", default="plain_bj,mixed_bj,mixed_mlp,plain_none",
                     help="comma list for --implicit: plain_bj, mixed_bj, plain_none, mixed_mlp")
+    ap.add_argument("--f32", action="store_true",
+                    help="time the FP32 fused residual + exact Jv (dg_jvp_f32) instead of the FP64 one")
     ap.add_argument("--precision", action="store_true",
                     help="contraction precision study (FP32 / bf16 / fp16 and split variants) instead")
     ap.add_argument("--mlp-steps", type=int, default=2, help="plain steps whose blocks train the network")
@@ -239,7 +241,10 @@ def main_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        mesh.jvp(ug, vg, t=0.0, out=jv, r_out=r)
+        if args.f32:
+            mesh.jvp_f32(ug, vg, t=0.0, out=jv, r_out=r)
+        else:
+            mesh.jvp(ug, vg, t=0.0, out=jv, r_out=r)
 
     for _ in range(args.warmup):
         step()
@@ -281,12 +286,12 @@ def main_ours(args):
     dom_name, (dom_ms, dom_cnt) = dom
     per_launch_ms = dom_ms / dom_cnt
     key = (dom_name, desc.p + 1)
-    fpe = FP64_FLOPS_PER_ELEMENT.get(key)
+    fpe = None if args.f32 else FP64_FLOPS_PER_ELEMENT.get(key)
     flops = fpe * mesh.n_elem if fpe else None
     achieved = flops / (per_launch_ms * 1e-3) / 1e12 if flops else None
     probe = DG.probe_fp64()
     fresh = residual_kernel_digest() == CAPTURE_DIGEST
-    traffic = DRAM_BYTES_PER_LAUNCH.get(key) if (args.config == CONFIG_NAME and fresh) else None
+    traffic = DRAM_BYTES_PER_LAUNCH.get(key) if (args.config == CONFIG_NAME and fresh and not args.f32) else None
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4) if achieved else None,
                 "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4) if achieved else None, "traffic": traffic,
@@ -341,9 +346,9 @@ def main_ours(args):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "vs_baseline": None, "dtype": "f32" if args.f32 else "f64", "data": "synthetic",
                "config": {"workload": f"{args.config}: {W.CONFIGS[args.config][1]}", "n_elem": mesh.n_elem,
-                          "p": desc.p, "n_dof": mesh.n_dof, "step": "fused residual + exact Jv (dg_jvp)",
+                          "p": desc.p, "n_dof": mesh.n_dof, "step": "fused residual + exact Jv (dg_jvp_f32)" if args.f32 else "fused residual + exact Jv (dg_jvp)",
                           "l2": "2x L2 buffer written between timed steps", "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                "kernels": {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items()},

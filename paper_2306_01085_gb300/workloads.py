@@ -192,6 +192,8 @@ CONFIGS = {
     # name: (descriptor factory, human description)
     "box4_p2": (lambda: box_desc(p=2, n=4), "periodic unit box 4x4x4, p=2, Re=100, Pr=0.7"),
     "shell16x8_p4": (lambda: shell_desc(n=16, nr=8, p=4), "cubed-sphere shell 6x16x16x8, p=4"),
+    "shell24x8_p2_euv": (lambda: shell_desc(n=24, nr=8, p=2, euv=True),
+                         "cubed-sphere shell 6x24x24x8, p=2, EUV (small profiling case, 3.7M DOF)"),
     "shell32x16_p2_euv": (lambda: shell_desc(n=32, nr=16, p=2, euv=True),
                           "cubed-sphere shell 6x32x32x16, p=2, EUV"),
     "shell32x16_p2_euvac": (lambda: shell_desc(n=32, nr=16, p=2, euvac=True, day=172.0),
