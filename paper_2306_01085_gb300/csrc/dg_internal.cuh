@@ -304,15 +304,18 @@ __device__ inline void primitives(const PhysT<R>& P, const S u[5], const S q[3][
 template <typename S, typename R = typename RealOf<S>::type>
 __device__ inline void flux_dot_n(const PhysT<R>& P, const S u[5], const S q[3][5], const R n[3], bool viscous,
                                   S out[5]) {
-  S isr = s_exp(R(-0.5) * u[0]);
-  S v[3] = {u[1] * isr, u[2] * isr, u[3] * isr};
-  S vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  Prim<S> w;
+  if (viscous) {
+    primitives(P, u, q, w);
+  } else {
+    w.isr = s_exp(R(-0.5) * u[0]);
+    for (int m = 0; m < 3; ++m) w.v[m] = u[1 + m] * w.isr;
+  }
+  S vn = w.v[0] * n[0] + w.v[1] * n[1] + w.v[2] * n[2];
   out[0] = u[0] * vn;
   for (int m = 0; m < 3; ++m) out[1 + m] = u[1 + m] * vn + (P.p_coef * n[m]) * u[4];
   out[4] = u[4] * vn;
   if (viscous) {
-    Prim<S> w;
-    primitives(P, u, q, w);
     S cm = (P.c_mu * w.mu) * w.isr;
     S ck = ((P.c_k / P.cv) * w.mu) * w.isr;
     for (int m = 0; m < 3; ++m)

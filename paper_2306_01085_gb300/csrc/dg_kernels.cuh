@@ -501,24 +501,23 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
   primitives(P, u, q, w);
   const S cm = (P.c_mu * w.mu) * w.isr;
   const S ck = ((P.c_k / P.cv) * w.mu) * w.isr;
-  S F[5][3];
+  // reference-space fluxes Fref[a][c] = sum_d G[a][d] F[c][d], formed from the contractions of the
+  // cofactor rows with v, grad T and the strain rows (F[c][d] = u_c v_d + p delta - viscous terms)
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    F[0][d] = u[0] * w.v[d];
-    F[4][d] = u[4] * w.v[d] - ck * w.gT[d];
+  for (int a = 0; a < 3; ++a) {
+    const R g0 = G[a * 3 + 0], g1 = G[a * 3 + 1], g2 = G[a * 3 + 2];
+    const S Gv = g0 * w.v[0] + g1 * w.v[1] + g2 * w.v[2];
+    const S GgT = g0 * w.gT[0] + g1 * w.gT[1] + g2 * w.gT[2];
+    Fref[a][0] = u[0] * Gv;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const S Ge = g0 * w.eps[m][0] + g1 * w.eps[m][1] + g2 * w.eps[m][2];
+      Fref[a][1 + m] = u[1 + m] * Gv + (P.p_coef * G[a * 3 + m]) * u[4] - cm * Ge;
+    }
+    Fref[a][4] = u[4] * Gv - ck * GgT;
   }
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) F[1 + m][d] = u[1 + m] * w.v[d] - cm * w.eps[m][d];
-#pragma unroll
-  for (int m = 0; m < 3; ++m) F[1 + m][m] = F[1 + m][m] + P.p_coef * u[4];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int c = 0; c < 5; ++c) Fref[a][c] = G[a * 3 + 0] * F[c][0] + G[a * 3 + 1] * F[c][1] + G[a * 3 + 2] * F[c][2];
   // source terms
-  const S sr = s_exp(R(0.5) * u[0]);
+  const S sr = s_inv(w.isr);
   const S wxv[3] = {P.omega[1] * w.v[2] - P.omega[2] * w.v[1], P.omega[2] * w.v[0] - P.omega[0] * w.v[2],
                     P.omega[0] * w.v[1] - P.omega[1] * w.v[0]};
   src[0] = (u[0] - R(1)) * w.div;
