@@ -105,22 +105,23 @@ def face_fluxes(mesh, u, q, elems, C):
         u_nb = np.moveaxis(_neighbour_traces(mesh, tu, elems, f), 0, 1)
         q_nb = np.moveaxis(_neighbour_traces(mesh, tq, elems, f).reshape(len(elems), 3, 5, mesh.Nf), 0, 2)
         nds = np.moveaxis(mesh.nF[elems, f], 0, 1)                              # (3, e, Nf)
+        xf = np.moveaxis(mesh.xF[elems, f], 0, 1)                               # (3, e, Nf)
         area = mesh.areaF[elems, f]                                              # (e, Nf)
         bc = mesh.bc[elems, f]
         # interior: central flux plus sigma (u - u_hat)
         uhat = 0.5 * (u_own + u_nb)
-        Fo = P.flux(u_own, q_own, C)
-        Fn = P.flux(u_nb, q_nb, C)
-        fh = 0.5 * np.einsum("cdef,def->cef", Fo + Fn, nds) + P.sigma(uhat, C) * (u_own - uhat) * area
+        Fo = P.flux(u_own, q_own, C, x=xf)
+        Fn = P.flux(u_nb, q_nb, C, x=xf)
+        fh = 0.5 * np.einsum("cdef,def->cef", Fo + Fn, nds) + P.sigma(uhat, C, xf) * (u_own - uhat) * area
         wall = bc == BC_WALL
         if np.any(wall):
             ub = P.wall_state(u_own[:, wall], C)
-            Fb = P.flux(ub, q_own[:, :, wall], C)
+            Fb = P.flux(ub, q_own[:, :, wall], C, x=xf[:, wall])
             fh[:, wall] = (np.einsum("cdef,def->cef", Fb, nds[:, wall])
-                           + P.sigma(ub, C) * (u_own[:, wall] - ub) * area[wall])
+                           + P.sigma(ub, C, xf[:, wall]) * (u_own[:, wall] - ub) * area[wall])
         out_ = bc == BC_OUTFLOW
         if np.any(out_):
-            Fi = P.flux(u_own[:, out_], q_own[:, :, out_], C, viscous=False)
+            Fi = P.flux(u_own[:, out_], q_own[:, :, out_], C, viscous=False, x=xf[:, out_])
             fh[:, out_] = np.einsum("cdef,def->cef", Fi, nds[:, out_])
         out.append(np.moveaxis(fh, 0, 1))
     return np.stack(out, axis=1)
@@ -141,7 +142,7 @@ def residual(mesh, u, q=None, t=0.0, elems=None):
     uG = np.moveaxis(np.einsum("gi,eci->ecg", mesh.phi, uE), 0, 1)               # (5, e, g)
     qG = np.moveaxis(np.einsum("gi,edci->edcg", mesh.phi, qE), 0, 2)             # (3, 5, e, g)
     xG = np.moveaxis(mesh.xG[elems], 0, 1)                                        # (3, e, g)
-    F = P.flux(uG, qG, C)                                                         # (5, 3, e, g)
+    F = P.flux(uG, qG, C, x=xG)                                                   # (5, 3, e, g)
     s = P.source(uG, qG, xG, t, C)                                                # (5, e, g)
     Wd = mesh.W[None, :] * mesh.detJ[elems]
     # (F, grad phi_i): sum_g Wd sum_d F_cd sum_a dphi[g, a, i] Jinv[g, a, d]

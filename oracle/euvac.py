@@ -42,29 +42,55 @@ C_LIGHT = 299792458.0         # m / s
 DELTA_0 = math.radians(23.44)
 ECC = 0.0167
 
-# wavelength band [A] (lo, hi; lo == hi for a line), F_74113 [1e13 m^-2 s^-1], A, phi_O [1e-22 m^2]
+# wavelength band [A] (lo, hi; lo == hi for a line), F_74113 [1e13 m^-2 s^-1], A, and the cross
+# sections [1e-22 m^2] of N2, O2, O, He
 TABLE = [
-    (50, 100, 1.200, 0.0100, 0.730), (100, 150, 0.450, 0.0071, 1.839), (150, 200, 4.800, 0.0134, 3.732),
-    (200, 250, 3.100, 0.0195, 5.202), (256.3, 256.3, 0.460, 0.0028, 6.050), (284.15, 284.15, 0.210, 0.1380, 7.080),
-    (250, 300, 1.679, 0.0265, 6.461), (303.31, 303.31, 0.800, 0.0250, 7.680), (303.78, 303.78, 6.900, 0.0033, 7.700),
-    (300, 350, 0.965, 0.0225, 8.693), (368.07, 368.07, 0.650, 0.0066, 9.840), (350, 400, 0.314, 0.0365, 9.687),
-    (400, 450, 0.383, 0.0074, 11.496), (465.22, 465.22, 0.290, 0.0075, 11.930), (450, 500, 0.285, 0.0202, 12.127),
-    (500, 550, 0.452, 0.0088, 12.059), (554.37, 554.37, 0.720, 0.0033, 12.590), (584.33, 584.33, 1.270, 0.0052, 13.090),
-    (550, 600, 0.357, 0.0037, 13.024), (609.76, 609.76, 0.530, 0.0162, 13.400), (629.73, 629.73, 1.590, 0.0033, 13.400),
-    (600, 650, 0.342, 0.0118, 13.365), (650, 700, 0.230, 0.0043, 17.245), (703.31, 703.31, 0.360, 0.0030, 11.460),
-    (700, 750, 0.141, 0.0047, 10.736), (765.15, 765.15, 0.170, 0.0039, 4.000), (770.41, 770.41, 0.260, 0.0128, 3.890),
-    (789.36, 789.36, 0.702, 0.0033, 3.749), (750, 800, 0.758, 0.0048, 5.091), (800, 850, 1.625, 0.0048, 3.498),
-    (850, 900, 3.537, 0.0057, 4.554), (900, 950, 3.000, 0.0050, 1.315), (977.02, 977.02, 4.400, 0.0039, 0.0),
-    (950, 1000, 1.475, 0.0044, 0.0), (1025.72, 1025.72, 3.500, 0.0052, 0.0), (1031.91, 1031.91, 2.100, 0.0053, 0.0),
-    (1000, 1050, 2.467, 0.0044, 0.0),
+    (50, 100, 1.200, 0.0100, 0.72, 1.316, 0.73, 0.144),
+    (100, 150, 0.450, 0.0071, 2.261, 3.806, 1.839, 0.479),
+    (150, 200, 4.800, 0.0134, 4.958, 7.509, 3.732, 1.157),
+    (200, 250, 3.100, 0.0195, 8.392, 10.9, 5.202, 1.601),
+    (256.3, 256.3, 0.460, 0.0028, 10.21, 13.37, 6.05, 2.121),
+    (284.15, 284.15, 0.210, 0.1380, 10.9, 15.79, 7.08, 2.595),
+    (250, 300, 1.679, 0.0265, 10.493, 14.387, 6.461, 2.321),
+    (303.31, 303.31, 0.800, 0.0250, 11.67, 16.8, 7.68, 2.953),
+    (303.78, 303.78, 6.900, 0.0033, 11.7, 16.81, 7.7, 2.962),
+    (300, 350, 0.965, 0.0225, 13.857, 17.438, 8.693, 3.544),
+    (368.07, 368.07, 0.650, 0.0066, 16.91, 18.32, 9.84, 4.268),
+    (350, 400, 0.314, 0.0365, 16.395, 18.118, 9.687, 4.142),
+    (400, 450, 0.383, 0.0074, 21.675, 20.31, 11.496, 5.447),
+    (465.22, 465.22, 0.290, 0.0075, 23.16, 21.91, 11.93, 6.563),
+    (450, 500, 0.285, 0.0202, 23.471, 23.101, 12.127, 7.208),
+    (500, 550, 0.452, 0.0088, 24.501, 24.606, 12.059, 0.958),
+    (554.37, 554.37, 0.720, 0.0033, 24.13, 26.04, 12.59, 0.0),
+    (584.33, 584.33, 1.270, 0.0052, 22.4, 22.72, 13.09, 0.0),
+    (550, 600, 0.357, 0.0037, 22.787, 26.61, 13.024, 0.0),
+    (609.76, 609.76, 0.530, 0.0162, 22.79, 28.07, 13.4, 0.0),
+    (629.73, 629.73, 1.590, 0.0033, 23.37, 32.06, 13.4, 0.0),
+    (600, 650, 0.342, 0.0118, 23.339, 26.017, 13.365, 0.0),
+    (650, 700, 0.230, 0.0043, 31.755, 21.919, 17.245, 0.0),
+    (703.31, 703.31, 0.360, 0.0030, 26.54, 27.44, 11.46, 0.0),
+    (700, 750, 0.141, 0.0047, 24.662, 28.535, 10.736, 0.0),
+    (765.15, 765.15, 0.170, 0.0039, 120.49, 20.8, 4, 0.0),
+    (770.41, 770.41, 0.260, 0.0128, 14.18, 18.91, 3.89, 0.0),
+    (789.36, 789.36, 0.702, 0.0033, 16.487, 26.668, 3.749, 0.0),
+    (750, 800, 0.758, 0.0048, 33.578, 22.145, 5.091, 0.0),
+    (800, 850, 1.625, 0.0048, 16.992, 16.631, 3.498, 0.0),
+    (850, 900, 3.537, 0.0057, 20.249, 8.562, 4.554, 0.0),
+    (900, 950, 3.000, 0.0050, 9.68, 12.817, 1.315, 0.0),
+    (977.02, 977.02, 4.400, 0.0039, 2.24, 18.73, 0.0, 0.0),
+    (950, 1000, 1.475, 0.0044, 50.988, 21.108, 0.0, 0.0),
+    (1025.72, 1025.72, 3.500, 0.0052, 0.0, 1.63, 0.0, 0.0),
+    (1031.91, 1031.91, 2.100, 0.0053, 0.0, 1.05, 0.0, 0.0),
+    (1000, 1050, 2.467, 0.0044, 0.0, 1.346, 0.0, 0.0),
 ]
+SPECIES_COLUMNS = {"N2": 4, "O2": 5, "O": 6, "He": 7}
 
 
-def bins():
-    """Arrays lambda [m] (band centre or line), F_74113 [m^-2 s^-1], A, phi_O [m^2]."""
+def bins(species="O"):
+    """Arrays lambda [m] (band centre or line), F_74113 [m^-2 s^-1], A, phi_species [m^2]."""
     t = np.array(TABLE, dtype=float)
     lam = 0.5 * (t[:, 0] + t[:, 1]) * 1e-10
-    return lam, t[:, 2] * 1e13, t[:, 3], t[:, 4] * 1e-22
+    return lam, t[:, 2] * 1e13, t[:, 3], t[:, SPECIES_COLUMNS[species]] * 1e-22
 
 
 def solar_flux(f107, f107a, d=1.0):
@@ -123,6 +149,24 @@ def heating_dimensional(rho, T, r, cchi, R0, m, g, eps, I0):
     return q
 
 
+def heating_absorbers(n_s, phi_s, T, r, cchi, R0, m, g, eps, I0):
+    """q_euv [W/m^3] for several absorbers: number densities n_s and cross-section arrays phi_s (per
+    species, per band); every band is attenuated by the optical depth summed over the species."""
+    lam = bins()[0]
+    H = 1.380649e-23 * T / (m * g)
+    ch = chapman(r / H, cchi, r / R0)
+    lit = np.isfinite(np.real(ch))
+    chl = np.where(lit, ch, 0.0)
+    q = 0.0
+    for j in range(len(lam)):
+        absorb = sum(n * ph[j] for n, ph in zip(n_s, phi_s))
+        if np.all(np.asarray(absorb) == 0):
+            continue
+        tau = absorb * H * chl
+        q = q + np.where(lit, eps * absorb * I0[j] * np.exp(-tau) * H_PLANCK * C_LIGHT / lam[j], 0.0)
+    return q
+
+
 def heating(u, x, t, C):
     """Nondimensional EUVAC heating Q* (multiplied by e^{-varrho/2}/c_v in the energy source), in
     the scaling of the Gaussian heating, q* = q H0 / (rho0 c_v0 T0 a0), with H0 = k_B T0/(m g0),
@@ -139,5 +183,12 @@ def heating(u, x, t, C):
     s = sun_direction(C.euv_day, C.euv_omega_t * t)
     cchi = np.clip((x[0] * s[0] + x[1] * s[1] + x[2] * s[2]) / r, -1.0, 1.0)
     I0 = solar_flux(C.euv_f107, C.euv_f107a, C.euv_dsun)
-    q = heating_dimensional(rho, T, r * H0, cchi, C.g_r0 * H0, m0 * C.m, g, C.euv_eff, I0)
+    if getattr(C, "comp", 0):
+        from . import composition as CM
+        mstar, _, _, _, chi = CM.mixture(x, C)
+        n_s = [rho * chi[k] / (m0 * CM.M_REL[k]) for k in range(4)]
+        phi_s = [bins(s)[3] for s in CM.SPECIES]
+        q = heating_absorbers(n_s, phi_s, T, r * H0, cchi, C.g_r0 * H0, m0 * mstar, g, C.euv_eff, I0)
+    else:
+        q = heating_dimensional(rho, T, r * H0, cchi, C.g_r0 * H0, m0 * C.m, g, C.euv_eff, I0)
     return q * H0 / (rho0 * cv0 * T0 * a0)

@@ -22,6 +22,7 @@ import math
 
 import numpy as np
 
+from . import composition as _comp
 from . import euvac as _euvac
 
 
@@ -51,11 +52,22 @@ class Coeffs:
         self.euv_width = desc.euv_width
         self.euv_omega_t = desc.euv_omega_t
         for k in ("euv_day", "euv_f107", "euv_f107a", "euv_eff", "euv_dsun", "ref_T0", "ref_rho0", "ref_m",
-                  "ref_g0"):
+                  "ref_g0", "comp", "eddy_nu", "eddy_alpha"):
             setattr(self, k, getattr(desc, k))
+        self.comp_a = np.array(desc.comp_a, dtype=np.float64).reshape(3, 2)
+        self.comp_b = np.array(desc.comp_b, dtype=np.float64).reshape(3, 2)
 
 
-def _transport(T, C):
+def _mixture(x, C):
+    """(m, c_v, grad c_v or None, kappa factor, mass fractions or None) at positions x."""
+    if C.comp and x is not None:
+        return _comp.mixture(x, C)
+    return C.m, C.cv, None, 1.0, None
+
+
+def _transport(T, C, u0=None, mix=None):
+    if C.comp:
+        return _comp.transport(T, u0, mix[0], mix[3], C)
     if C.visc_exp == 0.0:
         return np.ones_like(T), np.ones_like(T)
     mu = T ** C.visc_exp
@@ -77,11 +89,14 @@ def primitives(u, q, C):
     return sr, isr, v, T, gv, gT, div, eps
 
 
-def flux(u, q, C, viscous=True):
-    """Physical flux F[c, d] of Eq. fluxSWNondimensional (left-hand divergence terms)."""
+def flux(u, q, C, viscous=True, x=None):
+    """Physical flux F[c, d] of Eq. fluxSWNondimensional (left-hand divergence terms); x: positions
+    (needed with variable composition)."""
     sr, isr, v, T, gv, gT, div, eps = primitives(u, q, C)
-    mu, kappa = _transport(T, C)
-    p_coef = 1.0 / (C.gamma * C.m)
+    mix = _mixture(x, C)
+    mu, kappa = _transport(T, C, u[0], mix)
+    p_coef = 1.0 / (C.gamma * mix[0])
+    cv = mix[1]
     F = []
     F.append(np.stack([u[0] * v[d] for d in range(3)]))
     for m in range(3):
@@ -96,7 +111,7 @@ def flux(u, q, C, viscous=True):
     for d in range(3):
         val = u[4] * v[d]
         if viscous:
-            val = val - C.c_kappa * kappa * isr / C.cv * gT[d]
+            val = val - C.c_kappa * kappa * isr / cv * gT[d]
         row.append(val)
     F.append(np.stack(row))
     return np.stack(F)
@@ -138,31 +153,38 @@ def euv_heating(x, t, C):
 def source(u, q, x, t, C):
     """Source s(u, q) of Eq. fluxSWNondimensional (right-hand side)."""
     sr, isr, v, T, gv, gT, div, eps = primitives(u, q, C)
-    mu, kappa = _transport(T, C)
+    mix = _mixture(x, C)
+    mu, kappa = _transport(T, C, u[0], mix)
+    mm, cv, gcv = mix[0], mix[1], mix[2]
     a = acceleration(x, v, C)
     s = [(u[0] - 1.0) * div]
     for m in range(3):
         eps_grad = eps[m, 0] * q[0, 0] + eps[m, 1] * q[1, 0] + eps[m, 2] * q[2, 0]
-        s.append(sr * a[m] + 0.5 * div * u[1 + m] - 0.5 / (C.gamma * C.m) * u[4] * q[m, 0]
+        s.append(sr * a[m] + 0.5 * div * u[1 + m] - 0.5 / (C.gamma * mm) * u[4] * q[m, 0]
                  + 0.5 * C.c_mu * mu * isr * eps_grad)
     gT_grad = gT[0] * q[0, 0] + gT[1] * q[1, 0] + gT[2] * q[2, 0]
     diss = sum(eps[m, d] * gv[m, d] for m in range(3) for d in range(3))
     heat = _euvac.heating(u, x, t, C) if C.euv == 2 else euv_heating(x, t, C)
-    s.append(heat * isr / C.cv
-             + (1.5 - C.gamma) * u[4] * div
-             + 0.5 * C.c_kappa * kappa * isr / C.cv * gT_grad
-             + C.c_diss * mu * isr / C.cv * diss)
+    s4 = (heat * isr / cv
+          + (1.5 - C.gamma) * u[4] * div
+          + 0.5 * C.c_kappa * kappa * isr / cv * gT_grad
+          + C.c_diss * mu * isr / cv * diss)
+    if gcv is not None:
+        # -(1/c_v) (sqrt(rho) T v - c_kappa kappa / (sqrt(rho) c_v) grad T) . grad c_v
+        s4 = s4 - sum((u[4] * v[d] - C.c_kappa * kappa * isr / cv * gT[d]) * gcv[d] for d in range(3)) / cv
+    s.append(s4)
     return np.stack(s)
 
 
-def sigma(uhat, C):
+def sigma(uhat, C, x=None):
     """Diagonal of sigma = sigma_c + sigma_d of Eq. LDG2, evaluated at the trace state uhat."""
     isr = np.exp(-0.5 * uhat[0])
     T = uhat[4] * isr
-    mu, kappa = _transport(T, C)
+    mix = _mixture(x, C)
+    mu, kappa = _transport(T, C, uhat[0], mix)
     lam = C.lam * np.ones_like(uhat[0])
     sm = lam + C.c_mu * mu * isr
-    return np.stack([lam, sm, sm, sm, lam + C.c_kappa * kappa * isr / C.cv])
+    return np.stack([lam, sm, sm, sm, lam + C.c_kappa * kappa * isr / mix[1]])
 
 
 def wall_state(u, C):

@@ -89,6 +89,12 @@ class MeshDesc:
     ref_rho0: float = 0.0       # reference density [kg/m^3]
     ref_m: float = 0.0          # reference molecular mass [kg]
     ref_g0: float = 0.0         # reference gravity at the inner radius [m/s^2]
+    # variable composition (Sec. 2.1.1-2.1.2): comp = 1 turns it on
+    comp: int = 0
+    comp_a: tuple = (0.0,) * 6  # chi_s = sum_j a_j^s exp(b_j^s |r|) for N2, O2, He (|r| nondimensional),
+    comp_b: tuple = (0.0,) * 6  # row-major [species][j]; chi_O = 1 - the others
+    eddy_nu: float = 200.0      # nu_eddy / nu_0
+    eddy_alpha: float = 10.0    # alpha_eddy / alpha_0
 
     def as_dict(self):
         return asdict(self)
@@ -160,8 +166,23 @@ def box_desc(p=2, n=4, re=100.0, pr=0.7, bc_lo=BC_PERIODIC, bc_hi=BC_PERIODIC, g
                     visc_exp=visc_exp, gvec=(0.0, 0.0, -gravity))
 
 
+def synthetic_composition(ref: Reference, r_inner: float):
+    """Stand-in fit coefficients (a, b) [species N2, O2, He][j] for chi_s = sum_j a_j exp(b_j |r|), |r|
+    nondimensional (the paper fits MSIS output, which is not available): N2 0.76 e^{-z/110 km} +
+    0.02 e^{-z/30 km}, O2 0.19 e^{-z/75 km} + 0.01 e^{-z/25 km}, He 2e-6 e^{z/48 km}, z the height
+    above the inner boundary; atomic oxygen takes the rest (0.02 at 100 km, 0.93 at 600 km)."""
+    def term(frac, scale_km):
+        b = (1.0 if scale_km < 0 else -1.0) * ref.H0 / (abs(scale_km) * 1e3)
+        return frac * math.exp(-b * r_inner), b
+    pairs = [(term(0.76, 110.0), term(0.02, 30.0)), (term(0.19, 75.0), term(0.01, 25.0)), (term(2e-6, -48.0), (0.0, 0.0))]
+    a = tuple(p[j][0] for p in pairs for j in range(2))
+    b = tuple(p[j][1] for p in pairs for j in range(2))
+    return a, b
+
+
 def shell_desc(n=16, nr=8, p=4, euv=False, rotation=True, h_first_km=2.5, ref: Reference | None = None,
-               bc_lo=BC_WALL, bc_hi=BC_OUTFLOW, euvac=False, day=80.0, f107=150.0, f107a=150.0) -> MeshDesc:
+               bc_lo=BC_WALL, bc_hi=BC_OUTFLOW, euvac=False, day=80.0, f107=150.0, f107a=150.0,
+               composition=False) -> MeshDesc:
     """Cubed-sphere shell 100-600 km (Sec. 3.3) with the nondimensional numbers of Sec. 2.4."""
     ref = ref or shell_reference()
     H0 = ref.H0
@@ -185,6 +206,9 @@ def shell_desc(n=16, nr=8, p=4, euv=False, rotation=True, h_first_km=2.5, ref: R
         d.euv_omega_t = OMEGA_EARTH * ref.t0
         d.euv_day, d.euv_f107, d.euv_f107a = day, f107, f107a
     d.ref_T0, d.ref_rho0, d.ref_m, d.ref_g0 = ref.T0, ref.rho0, ref.m_O, ref.g0
+    if composition:
+        d.comp = 1
+        d.comp_a, d.comp_b = synthetic_composition(ref, r_in)
     return d
 
 

@@ -21,18 +21,19 @@ def _golden():
                 continue
             c = line.split()
             lo, _, hi = c[0].partition("-")
-            rows.append((float(lo), float(hi or lo), float(c[1]), float(c[2]), float(c[5])))
+            rows.append((float(lo), float(hi or lo), float(c[1]), float(c[2])) + tuple(float(v) for v in c[3:7]))
     return rows
 
 
 def test_table_matches_the_paper():
     g = _golden()
     assert len(g) == len(E.TABLE) == 37
-    for (lo, hi, F, A, phiO), (tlo, thi, tF, tA, tphi) in zip(g, E.TABLE):
+    for (lo, hi, F, A, *phis), (tlo, thi, tF, tA, *tphis) in zip(g, E.TABLE):
         assert (lo, hi) == (tlo, thi)
         assert math.isclose(F * 1e13, tF, rel_tol=1e-12)      # printed exponent -13, 1e13 meant
         assert math.isclose(A, tA, rel_tol=1e-12)
-        assert math.isclose(phiO, tphi * 1e-22, rel_tol=1e-12, abs_tol=1e-40)
+        for a, b in zip(phis, tphis):                          # N2, O2, O, He
+            assert math.isclose(a, b * 1e-22, rel_tol=1e-12, abs_tol=1e-40)
 
 
 def _column(rt, chi):

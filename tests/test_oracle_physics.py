@@ -66,10 +66,17 @@ def fd_div(fun, x, h=1e-3):
 
 
 def flux_of(x, C):
-    return P.flux(u_of(x), cs_grad(u_of, x), C)
+    return P.flux(u_of(x), cs_grad(u_of, x), C, x=x)
 
 
 def make_desc(kind):
+    if kind == "shell_comp":
+        d = make_desc("shell")
+        d.comp = 1
+        d.comp_a = (0.5, 0.1, 0.2, 0.05, 0.01, 0.0)     # N2, O2, He, varying over |r| in [1, 3]
+        d.comp_b = (-0.8, -2.0, -1.0, -3.0, 1.0, 0.0)
+        d.eddy_nu, d.eddy_alpha = 0.3, 0.2
+        return d
     if kind == "box":
         d = W.box_desc(p=2, n=2, re=50.0, pr=0.7, visc_exp=0.0)
         d.gvec = (0.1, -0.2, -1.0)
@@ -87,7 +94,20 @@ def make_desc(kind):
     return d
 
 
-@pytest.mark.parametrize("kind", ["box", "shell"])
+def _mix(y, d):
+    """m, c_v and the kappa factor of the composition fits at y, written from Sec. 2.1.1-2.1.2."""
+    r = np.sqrt((y ** 2).sum(0))
+    ms = [1.0, 1.75, 2.0, 0.25]
+    al = [1.0, 3.6 / 5.6, 3.6 / 5.6, 1.0]
+    ch = [d.comp_a[2 * s] * np.exp(d.comp_b[2 * s] * r) + d.comp_a[2 * s + 1] * np.exp(d.comp_b[2 * s + 1] * r)
+          for s in range(3)]
+    chi = [1.0 - ch[0] - ch[1] - ch[2]] + ch
+    moles = [chi[s] / ms[s] for s in range(4)]
+    tot = moles[0] + moles[1] + moles[2] + moles[3]
+    return 1.0 / tot, tot, sum(moles[s] * al[s] for s in range(4)) / tot
+
+
+@pytest.mark.parametrize("kind", ["box", "shell", "shell_comp"])
 def test_flux_form_reproduces_navier_stokes(kind):
     d = make_desc(kind)
     C = P.Coeffs(d)
@@ -109,11 +129,26 @@ def test_flux_form_reproduces_navier_stokes(kind):
     c_mu = 1.0 / math.sqrt(g * d.grashof)
     c_k = math.sqrt(g / d.grashof) / d.prandtl
     c_d = (g - 1.0) * math.sqrt(g / d.grashof)
-    m = d.mass
-    cv = 1.0 / m
+    comp = kind == "shell_comp"
 
-    def visc(T_):
+    def m_of(y):
+        return _mix(y, d)[0] if comp else d.mass
+
+    def cv_of(y):
+        return _mix(y, d)[1] if comp else 1.0 / d.mass
+
+    def visc(T_, y=None):
+        if comp:
+            return np.sqrt(T_ * m_of(y)) + d.eddy_nu * fields(y)[0]
         return T_ ** d.visc_exp if d.visc_exp else np.ones_like(T_)
+
+    def cond(T_, y=None):
+        if comp:
+            return _mix(y, d)[2] * T_ ** 0.69 + d.eddy_alpha * fields(y)[0] / m_of(y)
+        return visc(T_)
+
+    m = m_of(x)
+    cv = cv_of(x)
 
     def grad_v(y):
         return cs_grad(lambda z: fields(z)[1], y)            # [d, m] = d v_m / d x_d
@@ -125,10 +160,10 @@ def test_flux_form_reproduces_navier_stokes(kind):
                          for mm in range(3)])                 # [m, d]
 
     def tau(y):
-        return c_mu * visc(fields(y)[2]) * eps_of(y)          # (3, 3, n)
+        return c_mu * visc(fields(y)[2], y) * eps_of(y)       # (3, 3, n)
 
     def heat(y):
-        return (c_k * visc(fields(y)[2]) * cs_grad(lambda z: fields(z)[2][None], y)[:, 0])[None]
+        return (c_k * cond(fields(y)[2], y) * cs_grad(lambda z: fields(z)[2][None], y)[:, 0])[None]
 
     def mass_flux(y):
         r_, v_, _ = fields(y)
@@ -136,7 +171,7 @@ def test_flux_form_reproduces_navier_stokes(kind):
 
     Gv = grad_v(x)
     GT = cs_grad(lambda z: fields(z)[2][None], x)[:, 0]
-    p_of = lambda z: (fields(z)[0] * fields(z)[2] / (g * m))[None]
+    p_of = lambda z: (fields(z)[0] * fields(z)[2] / (g * m_of(z)))[None]
     Gp = cs_grad(p_of, x)[:, 0]
     div_v = Gv[0, 0] + Gv[1, 1] + Gv[2, 2]
     # acceleration a = g/gamma - Fr^2/gamma w x (w x r) - 2 Fr/sqrt(gamma) w x v
@@ -154,9 +189,13 @@ def test_flux_form_reproduces_navier_stokes(kind):
     vgradv = np.einsum("dn,dmn->mn", v, Gv)
     dv_ref = -vgradv - Gp / rho + fd_div(tau, x) / rho + a
     eps = eps_of(x)
-    dissip = np.einsum("mdn,dmn->n", visc(T)[None, None] * eps, Gv)
+    dissip = np.einsum("mdn,dmn->n", visc(T, x)[None, None] * eps, Gv)
+    # rho D(c_v T)/Dt with c_v(x): rho c_v DT/Dt + rho T v . grad c_v
+    vgcv = np.einsum("dn,dn->n", v, cs_grad(lambda z: np.atleast_2d(cv_of(z) * np.ones(z.shape[1:])), x)[:, 0]) \
+        if comp else 0.0
     dT_ref = -np.einsum("dn,dn->n", v, GT) + (
-        Q - g * (g - 1) * (rho * T / (g * m)) * div_v + fd_div(heat, x)[0] + c_d * dissip) / (rho * cv)
+        Q - g * (g - 1) * (rho * T / (g * m)) * div_v + fd_div(heat, x)[0] + c_d * dissip
+        - rho * T * vgcv) / (rho * cv)
 
     assert np.abs(drho - drho_ref).max() < 1e-8 * np.abs(drho_ref).max()
     assert np.abs(dv - dv_ref).max() < 1e-8 * np.abs(dv_ref).max()
