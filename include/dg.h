@@ -86,6 +86,19 @@ typedef struct dg_mesh_desc {
     double ref_rho0;       /* reference density [kg/m^3] */
     double ref_m;          /* reference molecular mass [kg] (m = ref_m * mass) */
     double ref_g0;         /* gravity at the radius g_r0 [m/s^2] */
+    /* Variable composition (Sec. 2.1.1-2.1.2), comp = 1: the mass fractions of N2, O2, He are
+     * chi_s = sum_{j<2} comp_a[2s+j] exp(comp_b[2s+j] |r|) (|r| nondimensional), chi_O = 1 - the others;
+     * m* = [sum_s chi_s/m_s*]^-1 and c_v* = 1/m* vary in space, the energy source gains
+     * -(1/c_v)(sqrt(rho) T v - c_kappa kappa/(sqrt(rho) c_v) grad T).grad c_v, the transport follows
+     * mu* = sqrt(T* m*) + eddy_nu rho*, kappa* = (sum_s x_s alpha_s/alpha_O) T*^0.69 + eddy_alpha rho* / m*
+     * (x_s number fractions, alpha_N2 = alpha_O2 = 3.6e-4, alpha_O = alpha_He = 5.6e-4; visc_exp and
+     * mass are not used), and EUVAC heating absorbs on all four species. */
+    int32_t comp;
+    int32_t reserved_comp; /* zero */
+    double comp_a[6];      /* [species N2, O2, He][term] */
+    double comp_b[6];
+    double eddy_nu;        /* nu_eddy / nu_0 */
+    double eddy_alpha;     /* alpha_eddy / alpha_0 */
 } dg_mesh_desc;
 
 /*

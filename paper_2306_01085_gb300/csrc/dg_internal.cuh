@@ -53,10 +53,21 @@ struct Phys {
   double cor;                     // 2 Fr / sqrt(gamma)
   int euv;
   double euv_amp, euv_inv2s2, euv_r_peak, euv_inv_w, euv_omega_t;
-  // EUVAC: Q* = (e^varrho/m*) sum_j b_j exp(-c_j e^varrho H* Ch / m*), H* = T* r*^2/(m* g_r0^2)
+  // EUVAC: with Phi_j = sum_s w_s phi_s^j (w_s = chi_s / m_s*, or 1/m* on oxygen for a constant
+  // composition), Q* = e^varrho sum_j B_j Phi_j exp(-tau_j), tau_j = euvac_cc e^varrho Phi_j H* Ch,
+  // H* = T* r*^2 / (m* g_r0^2)
   int n_euvac;
-  double euvac_b[40], euvac_c[40];
+  double euvac_B[40], euvac_phi[4][40], euvac_cc;
   double sun_cd, sun_sd, g_r0, inv_m;   // cos and sin of the declination, inner radius, 1/m*
+  // variable composition (Sec. 2.1.1-2.1.2)
+  int comp;
+  double comp_a[6], comp_b[6], eddy_nu, eddy_alpha, inv_gamma;
+};
+
+// mixture properties at one point: c_v* = 1/m* and the conductivity factor sum_s x_s alpha_s/alpha_O
+template <typename R>
+struct Mix {
+  R cv, kfac;
 };
 
 // --------------------------------------------------------------------------------------------
@@ -86,6 +97,7 @@ template <typename R>
 struct WorkT {
   R *ug, *uf, *qg, *qf, *fh, *qx;
   const R *geo, *fgeo, *acc, *xg;
+  const R *mixg, *mixf;   // variable composition at Gauss / face points (NULL without it)
 };
 struct Prof {
   bool on = false;
@@ -110,6 +122,8 @@ struct dg_mesh {
   double* acc = nullptr;   // [E][3][Np]: static acceleration g/gamma - Fr^2/gamma w x (w x r)
   double* xg = nullptr;    // [E][3][Np]: Gauss point positions
   double* fgeo = nullptr;  // [E][6][4][Nf]: w n dS (3), w |n dS| (1), outward, own face order
+  double* mixg = nullptr;  // [E][8][Np] variable composition at the Gauss points (desc.comp only)
+  double* mixf = nullptr;  // [E][6][2][Nf] variable composition at the face points
   int32_t* nbr = nullptr;  // [E][6]: neighbour element, or -bc_kind for a boundary face
   int32_t* nbr_fo = nullptr; // [E][6]: neighbour local face | orientation << 3
   int32_t* face_e = nullptr; // [F] owner element of each face visited once by the face kernel
@@ -167,6 +181,7 @@ struct Driver {
   static int q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s);
   static int mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
   static int mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
+  static int mixture(dg_mesh* m);
   // J_r probe restricted to each element's own diagonal block (exact, one column per element)
   static int jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s,
                           bool f32 = false);
@@ -256,8 +271,10 @@ struct PhysT {
   int euv;
   R euv_amp, euv_inv2s2, euv_r_peak, euv_inv_w, euv_omega_t;
   int n_euvac;
-  R euvac_b[40], euvac_c[40];
+  R euvac_B[40], euvac_phi[4][40], euvac_cc;
   R sun_cd, sun_sd, g_r0, inv_m;
+  int comp;
+  R comp_a[6], comp_b[6], eddy_nu, eddy_alpha, inv_gamma;
 };
 template <typename R>
 inline PhysT<R> phys_as(const Phys& P) {
@@ -269,10 +286,17 @@ inline PhysT<R> phys_as(const Phys& P) {
   q.euv_r_peak = (R)P.euv_r_peak; q.euv_inv_w = (R)P.euv_inv_w; q.euv_omega_t = (R)P.euv_omega_t;
   q.n_euvac = P.n_euvac;
   for (int j = 0; j < 40; ++j) {
-    q.euvac_b[j] = (R)P.euvac_b[j];
-    q.euvac_c[j] = (R)P.euvac_c[j];
+    q.euvac_B[j] = (R)P.euvac_B[j];
+    for (int s = 0; s < 4; ++s) q.euvac_phi[s][j] = (R)P.euvac_phi[s][j];
   }
+  q.euvac_cc = (R)P.euvac_cc;
   q.sun_cd = (R)P.sun_cd; q.sun_sd = (R)P.sun_sd; q.g_r0 = (R)P.g_r0; q.inv_m = (R)P.inv_m;
+  q.comp = P.comp;
+  for (int k = 0; k < 6; ++k) {
+    q.comp_a[k] = (R)P.comp_a[k];
+    q.comp_b[k] = (R)P.comp_b[k];
+  }
+  q.eddy_nu = (R)P.eddy_nu; q.eddy_alpha = (R)P.eddy_alpha; q.inv_gamma = (R)P.inv_gamma;
   return q;
 }
 
@@ -282,11 +306,24 @@ inline PhysT<R> phys_as(const Phys& P) {
 // --------------------------------------------------------------------------------------------
 template <typename S>
 struct Prim {
-  S isr, v[3], T, gv[3][3], gT[3], div, eps[3][3], mu;
+  S isr, v[3], T, gv[3][3], gT[3], div, eps[3][3], mu, kappa;
 };
 
 template <typename S, typename R = typename RealOf<S>::type>
-__device__ inline void primitives(const PhysT<R>& P, const S u[5], const S q[3][5], Prim<S>& w) {
+__device__ inline void transport(const PhysT<R>& P, const S& T, const S& isr, const Mix<R>& mx, S& mu, S& kappa) {
+  if (P.comp) {
+    // mu_m* = sqrt(T* m*), kappa_m* = kfac T*^0.69, plus the eddy offsets nu_e rho* and alpha_e rho* / m*
+    const S rho = s_inv(isr * isr);   // e^varrho
+    mu = s_sqrt(T * (R(1) / mx.cv)) + P.eddy_nu * rho;
+    kappa = mx.kfac * s_exp(R(0.69) * s_log(T)) + (P.eddy_alpha * mx.cv) * rho;
+  } else {
+    mu = (P.visc_exp != R(0)) ? s_exp(P.visc_exp * s_log(T)) : s_const<S>(R(1));
+    kappa = mu;
+  }
+}
+
+template <typename S, typename R = typename RealOf<S>::type>
+__device__ inline void primitives(const PhysT<R>& P, const S u[5], const S q[3][5], Prim<S>& w, const Mix<R>& mx) {
   w.isr = s_exp(R(-0.5) * u[0]);
   for (int m = 0; m < 3; ++m) w.v[m] = u[1 + m] * w.isr;
   w.T = u[4] * w.isr;
@@ -297,27 +334,28 @@ __device__ inline void primitives(const PhysT<R>& P, const S u[5], const S q[3][
   for (int m = 0; m < 3; ++m)
     for (int d = 0; d < 3; ++d) w.eps[m][d] = w.gv[m][d] + w.gv[d][m];
   for (int m = 0; m < 3; ++m) w.eps[m][m] = w.eps[m][m] - R(2.0 / 3.0) * w.div;
-  w.mu = (P.visc_exp != R(0)) ? s_exp(P.visc_exp * s_log(w.T)) : s_const<S>(R(1));
+  transport(P, w.T, w.isr, mx, w.mu, w.kappa);
 }
 
 // flux F(u, q) . n  (n: 3 reals), viscous terms optional
 template <typename S, typename R = typename RealOf<S>::type>
 __device__ inline void flux_dot_n(const PhysT<R>& P, const S u[5], const S q[3][5], const R n[3], bool viscous,
-                                  S out[5]) {
+                                  S out[5], const Mix<R>& mx) {
   Prim<S> w;
+  const R pc = P.comp ? mx.cv * P.inv_gamma : P.p_coef;   // 1/(gamma m*)
   if (viscous) {
-    primitives(P, u, q, w);
+    primitives(P, u, q, w, mx);
   } else {
     w.isr = s_exp(R(-0.5) * u[0]);
     for (int m = 0; m < 3; ++m) w.v[m] = u[1 + m] * w.isr;
   }
   S vn = w.v[0] * n[0] + w.v[1] * n[1] + w.v[2] * n[2];
   out[0] = u[0] * vn;
-  for (int m = 0; m < 3; ++m) out[1 + m] = u[1 + m] * vn + (P.p_coef * n[m]) * u[4];
+  for (int m = 0; m < 3; ++m) out[1 + m] = u[1 + m] * vn + (pc * n[m]) * u[4];
   out[4] = u[4] * vn;
   if (viscous) {
     S cm = (P.c_mu * w.mu) * w.isr;
-    S ck = ((P.c_k / P.cv) * w.mu) * w.isr;
+    S ck = ((P.c_k / (P.comp ? mx.cv : P.cv)) * w.kappa) * w.isr;
     for (int m = 0; m < 3; ++m)
       out[1 + m] = out[1 + m] - cm * (w.eps[m][0] * n[0] + w.eps[m][1] * n[1] + w.eps[m][2] * n[2]);
     out[4] = out[4] - ck * (w.gT[0] * n[0] + w.gT[1] * n[1] + w.gT[2] * n[2]);
@@ -326,16 +364,17 @@ __device__ inline void flux_dot_n(const PhysT<R>& P, const S u[5], const S q[3][
 
 // stabilisation diagonal sigma(u_hat) = lambda0 + sigma_d (Eq. LDG2)
 template <typename S, typename R = typename RealOf<S>::type>
-__device__ inline void sigma_diag(const PhysT<R>& P, const S uh[5], S sg[5]) {
+__device__ inline void sigma_diag(const PhysT<R>& P, const S uh[5], S sg[5], const Mix<R>& mx) {
   S isr = s_exp(R(-0.5) * uh[0]);
   S T = uh[4] * isr;
-  S mu = (P.visc_exp != R(0)) ? s_exp(P.visc_exp * s_log(T)) : s_const<S>(R(1));
+  S mu, kappa;
+  transport(P, T, isr, mx, mu, kappa);
   S sm = P.lam + (P.c_mu * mu) * isr;
   sg[0] = s_const<S>(P.lam);
   sg[1] = sm;
   sg[2] = sm;
   sg[3] = sm;
-  sg[4] = P.lam + ((P.c_k / P.cv) * mu) * isr;
+  sg[4] = P.lam + ((P.c_k / (P.comp ? mx.cv : P.cv)) * kappa) * isr;
 }
 
 template <typename S, typename R = typename RealOf<S>::type>

@@ -393,13 +393,14 @@ __device__ __forceinline__ void st(R* p, long long plane, DualT<R> v) {
 // F_hat . n = (F(u, q) + F(u2, q2)) . n / 2 + sigma(u_hat) (u - u_hat) |n|, u_hat = (u + u2) / 2
 template <typename S, typename R = typename RealOf<S>::type>
 __device__ __forceinline__ void face_flux_interior(const PhysT<R>& P, const S u[5], const S q[3][5], const S u2[5],
-                                                   const S q2[3][5], const R n[3], R area, S out[5]) {
+                                                   const S q2[3][5], const R n[3], R area, S out[5],
+                                                   const Mix<R>& mx) {
   S f1[5], fn[5], uh[5], sg[5];
-  flux_dot_n(P, u, q, n, true, f1);
-  flux_dot_n(P, u2, q2, n, true, fn);
+  flux_dot_n(P, u, q, n, true, f1, mx);
+  flux_dot_n(P, u2, q2, n, true, fn, mx);
 #pragma unroll
   for (int c = 0; c < 5; ++c) uh[c] = R(0.5) * (u[c] + u2[c]);
-  sigma_diag(P, uh, sg);
+  sigma_diag(P, uh, sg, mx);
 #pragma unroll
   for (int c = 0; c < 5; ++c) out[c] = R(0.5) * (f1[c] + fn[c]) + sg[c] * ((R(0.5) * area) * (u[c] - u2[c]));
 }
@@ -412,7 +413,7 @@ __global__ void k_faces(long long E, long long F, PhysT<R> P, const int* __restr
                         const int* __restrict__ face_f, const int* __restrict__ nbr,
                         const int* __restrict__ nbr_fo, const R* __restrict__ fgeo,
                         const R* __restrict__ uf, const R* __restrict__ qf,
-                        const R* __restrict__ qx, R* __restrict__ fh) {
+                        const R* __restrict__ qx, R* __restrict__ fh, const R* __restrict__ mixf) {
   using S = typename std::conditional<NC == 2, DualT<R>, R>::type;
   constexpr int NF = Shape<N>::NF;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -421,6 +422,11 @@ __global__ void k_faces(long long E, long long F, PhysT<R> P, const int* __restr
   const int f = (int)(idx % NF);
   const long long e = face_e[fi];
   const int phi = face_f[fi];
+  Mix<R> mx{P.cv, R(1)};
+  if (P.comp) {   // mixture at this face point: [E][6][2][NF] = (c_v*, conductivity factor)
+    mx.cv = mixf[((e * 6 + phi) * 2) * NF + f];
+    mx.kfac = mixf[((e * 6 + phi) * 2 + 1) * NF + f];
+  }
   const long long plane_u = E * 30 * NF, plane_q = E * 90 * NF;
   const R* gp = fgeo + ((e * 6 + phi) * 4) * NF + f;
   const R n[3] = {gp[0], gp[NF], gp[2 * NF]};
@@ -459,7 +465,7 @@ __global__ void k_faces(long long E, long long F, PhysT<R> P, const int* __restr
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int c = 0; c < 5; ++c) qa[d][c] = S{q2[d][c].v, qx[((long long)nb * 6 + phi2) * 15 * NF + (d * 5 + c) * NF + f2]};
-      face_flux_interior(P, u, q, ua, qa, n, area, out);
+      face_flux_interior(P, u, q, ua, qa, n, area, out, mx);
       // block of the neighbour: the own side carries only its cross gradient tangent
       S ub[5], qb[3][5], outb[5];
 #pragma unroll
@@ -468,23 +474,23 @@ __global__ void k_faces(long long E, long long F, PhysT<R> P, const int* __restr
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int c = 0; c < 5; ++c) qb[d][c] = S{q[d][c].v, qx[(e * 6 + phi) * 15 * NF + (d * 5 + c) * NF + f]};
-      face_flux_interior(P, ub, qb, u2, q2, n, area, outb);
+      face_flux_interior(P, ub, qb, u2, q2, n, area, outb, mx);
 #pragma unroll
       for (int c = 0; c < 5; ++c) st(fh + ob2 + c * NF, plane_u, -outb[c]);
     } else {
-      face_flux_interior(P, u, q, u2, q2, n, area, out);
+      face_flux_interior(P, u, q, u2, q2, n, area, out, mx);
 #pragma unroll
       for (int c = 0; c < 5; ++c) st(fh + ob2 + c * NF, plane_u, -out[c]);
     }
   } else if (nb == -DG_BC_WALL) {
     S ubd[5], sg[5];
     wall_trace(P, u, ubd);
-    flux_dot_n(P, ubd, q, n, true, out);
-    sigma_diag(P, ubd, sg);
+    flux_dot_n(P, ubd, q, n, true, out, mx);
+    sigma_diag(P, ubd, sg, mx);
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[c] = out[c] + sg[c] * (area * (u[c] - ubd[c]));
   } else {
-    flux_dot_n(P, u, q, n, false, out);
+    flux_dot_n(P, u, q, n, false, out, mx);
   }
 #pragma unroll
   for (int c = 0; c < 5; ++c) st(fh + ub + c * NF, plane_u, out[c]);
@@ -496,11 +502,15 @@ __global__ void k_faces(long long E, long long F, PhysT<R> P, const int* __restr
 template <typename S, typename R = typename RealOf<S>::type>
 __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], const S q[3][5],
                                              const R G[9], R Wd, const R acc[3],
-                                             const R* xg, R t, S Fref[3][5], S src[5]) {
+                                             const R* xg, R t, S Fref[3][5], S src[5], const R mg[8]) {
+  // mg (variable composition): c_v*, grad c_v* (3), conductivity factor, mass fractions of N2, O2, He
+  const Mix<R> mx{P.comp ? mg[0] : P.cv, P.comp ? mg[4] : R(1)};
+  const R cvp = mx.cv;
+  const R pcoef = P.comp ? cvp * P.inv_gamma : P.p_coef;   // 1/(gamma m*)
   Prim<S> w;
-  primitives(P, u, q, w);
+  primitives(P, u, q, w, mx);
   const S cm = (P.c_mu * w.mu) * w.isr;
-  const S ck = ((P.c_k / P.cv) * w.mu) * w.isr;
+  const S ck = ((P.c_k / cvp) * w.kappa) * w.isr;
   // reference-space fluxes Fref[a][c] = sum_d G[a][d] F[c][d], formed from the contractions of the
   // cofactor rows with v, grad T and the strain rows (F[c][d] = u_c v_d + p delta - viscous terms)
 #pragma unroll
@@ -512,7 +522,7 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const S Ge = g0 * w.eps[m][0] + g1 * w.eps[m][1] + g2 * w.eps[m][2];
-      Fref[a][1 + m] = u[1 + m] * Gv + (P.p_coef * G[a * 3 + m]) * u[4] - cm * Ge;
+      Fref[a][1 + m] = u[1 + m] * Gv + (pcoef * G[a * 3 + m]) * u[4] - cm * Ge;
     }
     Fref[a][4] = u[4] * Gv - ck * GgT;
   }
@@ -525,7 +535,7 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
   for (int m = 0; m < 3; ++m) {
     const S a_m = acc[m] - P.cor * wxv[m];
     const S eg = w.eps[m][0] * q[0][0] + w.eps[m][1] * q[1][0] + w.eps[m][2] * q[2][0];
-    src[1 + m] = sr * a_m + R(0.5) * (w.div * u[1 + m]) - (R(0.5) * P.p_coef) * (u[4] * q[m][0]) + R(0.5) * (cm * eg);
+    src[1 + m] = sr * a_m + R(0.5) * (w.div * u[1 + m]) - (R(0.5) * pcoef) * (u[4] * q[m][0]) + R(0.5) * (cm * eg);
   }
   const S tg = w.gT[0] * q[0][0] + w.gT[1] * q[1][0] + w.gT[2] * q[2][0];
   S diss = s_zero<S>();
@@ -533,7 +543,13 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int d = 0; d < 3; ++d) diss = diss + w.eps[m][d] * w.gv[m][d];
-  S s4 = (R(1.5) - P.gamma) * (u[4] * w.div) + R(0.5) * (ck * tg) + ((P.c_d / P.cv) * w.mu) * (w.isr * diss);
+  S s4 = (R(1.5) - P.gamma) * (u[4] * w.div) + R(0.5) * (ck * tg) + ((P.c_d / cvp) * w.mu) * (w.isr * diss);
+  if (P.comp) {
+    // -(1/c_v) (sqrt(rho) T v - c_kappa kappa / (sqrt(rho) c_v) grad T) . grad c_v
+    const S vg = w.v[0] * mg[1] + w.v[1] * mg[2] + w.v[2] * mg[3];
+    const S tgc = w.gT[0] * mg[1] + w.gT[1] * mg[2] + w.gT[2] * mg[3];
+    s4 = s4 - (u[4] * vg - ck * tgc) * (R(1) / cvp);
+  }
   if (P.euv == DG_EUV_GAUSS) {
     const R r = sqrt(xg[0] * xg[0] + xg[1] * xg[1] + xg[2] * xg[2]);
     const R sx = cos(P.euv_omega_t * t), sy = -sin(P.euv_omega_t * t);
@@ -542,7 +558,7 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
     const R chi = acos(cchi);
     const R dz = (r - P.euv_r_peak) * P.euv_inv_w;
     const R Qh = P.euv_amp * s_exp(-chi * chi * P.euv_inv2s2) * s_exp(R(-0.6931471805599453) * dz * dz);
-    s4 = s4 + (Qh / P.cv) * w.isr;
+    s4 = s4 + (Qh / cvp) * w.isr;
   } else if (P.euv == DG_EUV_EUVAC) {
     // EUVAC photoabsorption with Smith & Smith Chapman depths (Sec. 2.2)
     const R r = sqrt(xg[0] * xg[0] + xg[1] * xg[1] + xg[2] * xg[2]);
@@ -552,18 +568,31 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
     const R schi = sqrt(fmax(R(0), R(1) - cchi * cchi));
     if (cchi > R(0) || schi * r > P.g_r0) {          // not in the Earth's shadow
       const S er = sr * sr;                             // e^varrho
-      const S Hs = w.T * (r * r * P.inv_m / (P.g_r0 * P.g_r0));   // H* = T* r*^2 / (m* g_r0^2)
+      const R minv = P.comp ? cvp : P.inv_m;            // 1/m*
+      const S Hs = w.T * (r * r * minv / (P.g_r0 * P.g_r0));   // H* = T* r*^2 / (m* g_r0^2)
       const S rt = r * s_inv(Hs);                       // r~ = |r| / H
       const S ex = s_erfcx(s_sqrt(R(0.5) * rt) * fabs(cchi));
       const S base = s_sqrt(R(1.5707963267948966) * rt);
       S ch;
       if (cchi > R(0)) ch = base * ex;
       else ch = base * (R(2) * s_exp(rt * (R(1) - schi)) - ex);
-      const S k = er * Hs * ch * P.inv_m;              // tau_j = c_j k
+      // species weights w_s = chi_s / m_s* (O, N2, O2, He), or 1/m* on oxygen alone
+      R ws[4] = {P.inv_m, R(0), R(0), R(0)};
+      if (P.comp) {
+        ws[0] = (R(1) - mg[5] - mg[6] - mg[7]);
+        ws[1] = mg[5] * R(16.0 / 28.0);
+        ws[2] = mg[6] * R(16.0 / 32.0);
+        ws[3] = mg[7] * R(16.0 / 4.0);
+      }
+      const S k = (P.euvac_cc * er) * Hs * ch;          // tau_j = Phi_j k
       S qs = s_zero<S>();
 #pragma unroll 1
-      for (int j = 0; j < P.n_euvac; ++j) qs = qs + P.euvac_b[j] * s_exp(-P.euvac_c[j] * k);
-      s4 = s4 + (er * qs) * (P.inv_m / P.cv) * w.isr;
+      for (int j = 0; j < P.n_euvac; ++j) {
+        const R Phi = ws[0] * P.euvac_phi[0][j] + ws[1] * P.euvac_phi[1][j] + ws[2] * P.euvac_phi[2][j] +
+                      ws[3] * P.euvac_phi[3][j];
+        qs = qs + (P.euvac_B[j] * Phi) * s_exp(-Phi * k);
+      }
+      s4 = s4 + (er * qs) * (R(1) / cvp) * w.isr;
     }
   }
   src[4] = s4;
@@ -573,12 +602,16 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
 
 // stage_c != 0 (NC = 2): the tangent output is the DIRK stage operator J_G v = M v - stage_c J_r v,
 // M v = B^T (W B v) being formed from the tangent's own Gauss values
+// FP32: two CTAs per SM, since the value + tangent physics would otherwise take enough registers to
+// halve the resident warps of this latency-bound kernel (FP64 is bound by its pipe instead)
 template <int N, int NC, typename R, int CM = CM_NATIVE>
-__global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
+__global__ void __launch_bounds__(Epb<N, NC>::value * Shape<N>::NP, sizeof(R) == 4 ? 2 : 1)
+k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
                          const R* __restrict__ geo, const R* __restrict__ accg,
                          const R* __restrict__ xg, const R* __restrict__ ug,
                          const R* __restrict__ qg, const R* __restrict__ fh,
-                         double* __restrict__ r, double* __restrict__ jv, R stage_c) {
+                         double* __restrict__ r, double* __restrict__ jv, R stage_c,
+                         const R* __restrict__ mixg) {
   using S = typename std::conditional<NC == 2, DualT<R>, R>::type;
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
   __shared__ SmemOpsT<R> so;
@@ -627,7 +660,12 @@ __global__ void k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R
       x3[2] = xg[e * 3 * NP + 2 * NP + g];
     }
     S Fref[3][5];
-    volume_point<S>(P, u, q, G, Wd, a3, x3, t, Fref, srcv);
+    R mg[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    if (P.comp) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) mg[k] = mixg[(e * 8 + k) * NP + g];
+    }
+    volume_point<S>(P, u, q, G, Wd, a3, x3, t, Fref, srcv, mg);
     if constexpr (NC == 2) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) wu[c] = Wd * u[c].d;
@@ -749,6 +787,68 @@ __global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, co
       for (int k = 0; k < N; ++k) acc = fma(ev[k], in[(l * C + c) * NP + face_vol_point<N>(phi, f, k)], acc);
       traces[e * 6 * C * NF + rem] = acc;
     }
+  }
+}
+
+// variable composition (Sec. 2.1.1-2.1.2) at the Gauss and face points from the positions xg:
+// mixg [E][8][NP] = (c_v*, grad c_v* (3), conductivity factor, chi_N2, chi_O2, chi_He),
+// mixf [E][6][2][NF] = (c_v*, conductivity factor); face positions are the exact extrapolation of
+// the Gauss-point positions (the map is a polynomial of degree p)
+__device__ inline void mixture_at(const Phys& P, const double x[3], double out[8]) {
+  const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  const double inv_ms[4] = {1.0, 16.0 / 28.0, 16.0 / 32.0, 16.0 / 4.0};      // m_O / m_s
+  const double alpha[4] = {1.0, 3.6 / 5.6, 3.6 / 5.6, 1.0};                  // alpha_s / alpha_O
+  double chi[4], dchi[4];
+  chi[0] = 1.0;
+  dchi[0] = 0.0;
+  for (int s = 0; s < 3; ++s) {
+    double c = 0.0, dc = 0.0;
+    for (int j = 0; j < 2; ++j) {
+      const double t = P.comp_a[2 * s + j] * exp(P.comp_b[2 * s + j] * r);
+      c += t;
+      dc += P.comp_b[2 * s + j] * t;
+    }
+    chi[1 + s] = c;
+    dchi[1 + s] = dc;
+    chi[0] -= c;
+    dchi[0] -= dc;
+  }
+  double cv = 0.0, dcv = 0.0, ka = 0.0;
+  for (int s = 0; s < 4; ++s) {
+    cv += chi[s] * inv_ms[s];
+    dcv += dchi[s] * inv_ms[s];
+    ka += chi[s] * inv_ms[s] * alpha[s];
+  }
+  out[0] = cv;
+  for (int d = 0; d < 3; ++d) out[1 + d] = dcv * x[d] / r;
+  out[4] = ka / cv;
+  out[5] = chi[1];
+  out[6] = chi[2];
+  out[7] = chi[3];
+}
+
+template <int N>
+__global__ void k_mixture(long long E, const Ops* __restrict__ ops, Phys P, const double* __restrict__ xg,
+                          double* __restrict__ mixg, double* __restrict__ mixf) {
+  constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF;
+  const long long e = blockIdx.x;
+  if (e >= E) return;
+  for (int g = threadIdx.x; g < NP; g += blockDim.x) {
+    const double x[3] = {xg[(e * 3 + 0) * NP + g], xg[(e * 3 + 1) * NP + g], xg[(e * 3 + 2) * NP + g]};
+    double o[8];
+    mixture_at(P, x, o);
+    for (int k = 0; k < 8; ++k) mixg[(e * 8 + k) * NP + g] = o[k];
+  }
+  for (int idx = threadIdx.x; idx < 6 * NF; idx += blockDim.x) {
+    const int phi = idx / NF, f = idx % NF;
+    const double* ev = (phi & 1) ? ops->eR : ops->eL;
+    double x[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < 3; ++d)
+      for (int k = 0; k < N; ++k) x[d] = fma(ev[k], xg[(e * 3 + d) * NP + face_vol_point<N>(phi, f, k)], x[d]);
+    double o[8];
+    mixture_at(P, x, o);
+    mixf[((e * 6 + phi) * 2) * NF + f] = o[0];
+    mixf[((e * 6 + phi) * 2 + 1) * NF + f] = o[4];
   }
 }
 
@@ -924,7 +1024,8 @@ struct Smem {
 
 template <typename R> inline WorkT<R> work_of(dg_mesh* m);
 template <> inline WorkT<double> work_of<double>(dg_mesh* m) {
-  return WorkT<double>{m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf, m->ws.fh, m->ws.qx, m->geo, m->fgeo, m->acc, m->xg};
+  return WorkT<double>{m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf, m->ws.fh, m->ws.qx, m->geo, m->fgeo, m->acc, m->xg,
+                       m->mixg, m->mixf};
 }
 template <> inline WorkT<float> work_of<float>(dg_mesh* m) { return m->w32; }
 
@@ -975,7 +1076,7 @@ static int run_faces(dg_mesh* m, cudaStream_t s) {
   const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_FACES);
   k_faces<N, NC, BLK, R><<<blocks, threads, 0, s>>>(m->E, m->nfaces, phys_as<R>(m->phys), m->face_e, m->face_f,
-                                                     m->nbr, m->nbr_fo, w.fgeo, w.uf, w.qf, w.qx, w.fh);
+                                                     m->nbr, m->nbr_fo, w.fgeo, w.uf, w.qf, w.qx, w.fh, w.mixf);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_faces");
   return DG_OK;
@@ -991,7 +1092,7 @@ static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t 
   const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_VOLUME);
   k_volume<N, NC, R, CM><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), (R)t, w.geo, w.acc, w.xg,
-                                                   w.ug, w.qg, w.fh, r, jv, (R)stage_c);
+                                                   w.ug, w.qg, w.fh, r, jv, (R)stage_c, w.mixg);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_volume");
   return DG_OK;
@@ -1117,6 +1218,13 @@ int Driver<N>::q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) {
                                                                                    nullptr, m->ws.qf);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_tensor(q gauss)");
+  return DG_OK;
+}
+
+template <int N>
+int Driver<N>::mixture(dg_mesh* m) {
+  k_mixture<N><<<(unsigned)m->E, 128>>>(m->E, m->d_ops, m->phys, m->xg, m->mixg, m->mixf);
+  DG_LAUNCH_CHECK("k_mixture");
   return DG_OK;
 }
 

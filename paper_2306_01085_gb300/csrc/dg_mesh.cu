@@ -41,6 +41,7 @@ static int drv_residual(dg_mesh* m, const double* u, const double* v, double t, 
 static int drv_q_to_nodal(dg_mesh* m, double* q, cudaStream_t s) { DG_DISPATCH(m, q_to_nodal(m, q, s)); }
 static int drv_q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) { DG_DISPATCH(m, q_from_nodal(m, q, s)); }
 static int drv_mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s) { DG_DISPATCH(m, mass(m, v, mv, s)); }
+static int drv_mixture(dg_mesh* m) { DG_DISPATCH(m, mixture(m)); }
 static int drv_mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s) {
   DG_DISPATCH(m, mass_inv(m, v, mv, s));
 }
@@ -49,9 +50,10 @@ static int drv_mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s)
 // radial layers with geometric growth from the first-layer height (Sec. 3.3)
 // ------------------------------------------------------------------------------------------
 // Per-band coefficients of the EUVAC heating in the nondimensional variables (DG_EUV_EUVAC in
-// dg.h): with n = rho0 e^varrho / (m0 m*) and H = H0 H*, q* = q H0/(rho0 c_v0 T0 a0) =
-// (e^varrho/m*) sum_j b_j exp(-tau_j), tau_j = c_j e^varrho H* Ch / m*, where
-// b_j = eps phi_j I0_j (h c/lambda_j) H0 / (m0 c_v0 T0 a0) and c_j = rho0 phi_j H0 / m0.
+// dg.h). The absorbers' number densities are n_s = rho0 e^varrho w_s / m0 with w_s = chi_s / m_s*
+// (or 1/m* for the single constituent), so with Phi_j = sum_s w_s phi_s^j and H = H0 H*,
+// q* = q H0/(rho0 c_v0 T0 a0) = e^varrho sum_j B_j Phi_j exp(-tau_j), tau_j = cc e^varrho Phi_j H* Ch,
+// B_j = eps I0_j (h c/lambda_j) H0 / (m0 c_v0 T0 a0) and cc = rho0 H0 / m0.
 static bool euvac_coefficients(const dg_mesh_desc& d, Phys& P) {
   if (!(d.ref_T0 > 0 && d.ref_rho0 > 0 && d.ref_m > 0 && d.ref_g0 > 0 && d.euv_dsun > 0 && d.g_r0 > 0 &&
         d.mass > 0 && d.gamma > 1))
@@ -64,15 +66,15 @@ static bool euvac_coefficients(const dg_mesh_desc& d, Phys& P) {
   int n = 0;
   for (int j = 0; j < kEuvacRows && n < 40; ++j) {
     const EuvacRow& row = kEuvac[j];
-    if (row.phi_o == 0.0) continue;
     const double lambda = 0.5 * (row.lo + row.hi) * 1e-10;
     const double I0 = row.flux * 1e13 * std::max(0.8, 1.0 + row.a * (fbar - 80.0)) / (d.euv_dsun * d.euv_dsun);
-    const double phi = row.phi_o * 1e-22;
-    P.euvac_b[n] = d.euv_eff * phi * I0 * (h * c / lambda) * H0 / (d.ref_m * cv0 * d.ref_T0 * a0);
-    P.euvac_c[n] = d.ref_rho0 * phi * H0 / d.ref_m;
+    P.euvac_B[n] = d.euv_eff * I0 * (h * c / lambda) * H0 / (d.ref_m * cv0 * d.ref_T0 * a0);
+    const double phis[4] = {row.phi_o, row.phi_n2, row.phi_o2, row.phi_he};   // O, N2, O2, He
+    for (int s = 0; s < 4; ++s) P.euvac_phi[s][n] = phis[s] * 1e-22;
     ++n;
   }
   P.n_euvac = n;
+  P.euvac_cc = d.ref_rho0 * H0 / d.ref_m;
   const double w = 2.0 * M_PI / 365.24;
   const double delta = std::asin(std::sin(-23.44 * M_PI / 180.0) *
                                  std::cos(w * (d.euv_day + 9.0) + 2.0 * 0.0167 * std::sin(w * (d.euv_day - 3.0))));
@@ -319,7 +321,8 @@ static void free_mesh(dg_mesh* m) {
   dg_solver_release(m);
   dg_mlp_release(m);
   if (m->w32_base) cudaFree(m->w32_base);
-  void* ptrs[] = {m->d_ops, m->x, m->geo, m->acc, m->xg, m->fgeo, m->nbr, m->nbr_fo, m->face_e, m->face_f,
+  void* ptrs[] = {m->d_ops, m->x, m->geo, m->acc, m->xg, m->fgeo, m->mixg, m->mixf, m->nbr, m->nbr_fo, m->face_e,
+                  m->face_f,
                   m->ws.ug, m->ws.uf, m->ws.qg, m->ws.qf, m->ws.fh, m->ws.tmp, m->ws.red, m->ws.qx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -353,8 +356,10 @@ __global__ void k_to_f32(long long n, const double* __restrict__ x, float* __res
 int ensure_f32(dg_mesh* m) {
   if (m->w32_base) return DG_OK;
   const long long E = m->E, NP = m->np, NF = m->nf;
-  const long long sizes[10] = {2 * E * 5 * NP, 2 * E * 30 * NF, 2 * E * 15 * NP, 2 * E * 90 * NF, 2 * E * 30 * NF,
-                               E * 90 * NF,    E * 10 * NP,     E * 24 * NF,     E * 3 * NP,      E * 3 * NP};
+  const long long nmg = m->mixg ? E * 8 * NP : 0, nmf = m->mixf ? E * 12 * NF : 0;
+  const long long sizes[12] = {2 * E * 5 * NP, 2 * E * 30 * NF, 2 * E * 15 * NP, 2 * E * 90 * NF, 2 * E * 30 * NF,
+                               E * 90 * NF,    E * 10 * NP,     E * 24 * NF,     E * 3 * NP,      E * 3 * NP,
+                               nmg,            nmf};
   long long total = 0;
   for (long long z : sizes) total += (z + 63) / 64 * 64;
   cudaError_t err = cudaMalloc(&m->w32_base, sizeof(float) * (size_t)total);
@@ -362,15 +367,17 @@ int ensure_f32(dg_mesh* m) {
     m->w32_base = nullptr;
     return fail(DG_ENOMEM, std::string("FP32 workspace: ") + cudaGetErrorString(err));
   }
-  float* p[10];
+  float* p[12];
   long long off = 0;
-  for (int k = 0; k < 10; ++k) {
+  for (int k = 0; k < 12; ++k) {
     p[k] = m->w32_base + off;
     off += (sizes[k] + 63) / 64 * 64;
   }
-  m->w32 = WorkT<float>{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9]};
-  const double* src[4] = {m->geo, m->fgeo, m->acc, m->xg};
-  for (int k = 0; k < 4; ++k) {
+  m->w32 = WorkT<float>{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9],
+                        m->mixg ? p[10] : nullptr, m->mixf ? p[11] : nullptr};
+  const double* src[6] = {m->geo, m->fgeo, m->acc, m->xg, m->mixg, m->mixf};
+  for (int k = 0; k < 6; ++k) {
+    if (!src[k]) continue;
     k_to_f32<<<1024, 256>>>(sizes[6 + k], src[k], p[6 + k]);
     err = cudaGetLastError();
     if (err != cudaSuccess) return fail(DG_ECUDA, std::string("k_to_f32: ") + cudaGetErrorString(err));
@@ -427,6 +434,14 @@ extern "C" int dg_mesh_create(const dg_mesh_desc* desc, const double* nodes, dg_
   P.euv_r_peak = d.euv_r_peak;
   P.euv_inv_w = d.euv == DG_EUV_GAUSS ? 1.0 / d.euv_width : 0.0;
   P.euv_omega_t = d.euv_omega_t;
+  P.comp = d.comp;
+  for (int k = 0; k < 6; ++k) {
+    P.comp_a[k] = d.comp_a[k];
+    P.comp_b[k] = d.comp_b[k];
+  }
+  P.eddy_nu = d.eddy_nu;
+  P.eddy_alpha = d.eddy_alpha;
+  P.inv_gamma = 1.0 / d.gamma;
   P.n_euvac = 0;
   if (d.euv == DG_EUV_EUVAC && !euvac_coefficients(d, P)) {
     delete m;
@@ -508,6 +523,10 @@ extern "C" int dg_mesh_create(const dg_mesh_desc* desc, const double* nodes, dg_
     return fail(DG_ECUDA, std::string("dg_mesh_create upload: ") + cudaGetErrorString(err));
   }
   rc = drv_geometry(m, 0);
+  if (rc == DG_OK && d.comp) {
+    rc = dalloc(&m->mixg, E * 8 * NP) | dalloc(&m->mixf, E * 12 * NF);
+    if (rc == DG_OK) rc = drv_mixture(m);
+  }
   if (rc == DG_OK) err = cudaDeviceSynchronize();
   if (rc != DG_OK || err != cudaSuccess) {
     free_mesh(m);

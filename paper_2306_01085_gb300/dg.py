@@ -35,6 +35,8 @@ class DgMeshDesc(ctypes.Structure):
         ("euv_day", ctypes.c_double), ("euv_f107", ctypes.c_double), ("euv_f107a", ctypes.c_double),
         ("euv_eff", ctypes.c_double), ("euv_dsun", ctypes.c_double), ("ref_T0", ctypes.c_double),
         ("ref_rho0", ctypes.c_double), ("ref_m", ctypes.c_double), ("ref_g0", ctypes.c_double),
+        ("comp", ctypes.c_int32), ("reserved_comp", ctypes.c_int32), ("comp_a", ctypes.c_double * 6),
+        ("comp_b", ctypes.c_double * 6), ("eddy_nu", ctypes.c_double), ("eddy_alpha", ctypes.c_double),
     ]
 
 
@@ -131,8 +133,10 @@ def _check(rc):
 def to_c_desc(desc: W.MeshDesc) -> DgMeshDesc:
     c = DgMeshDesc()
     for name, _ in DgMeshDesc._fields_:
+        if name == "reserved_comp":
+            continue
         val = getattr(desc, name)
-        if name in ("gvec", "omega"):
+        if name in ("gvec", "omega", "comp_a", "comp_b"):
             getattr(c, name)[:] = [float(x) for x in val]
         else:
             setattr(c, name, val)

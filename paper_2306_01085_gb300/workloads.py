@@ -222,6 +222,9 @@ CONFIGS = {
                           "cubed-sphere shell 6x32x32x16, p=2, EUV"),
     "shell32x16_p2_euvac": (lambda: shell_desc(n=32, nr=16, p=2, euvac=True, day=172.0),
                             "cubed-sphere shell 6x32x32x16, p=2, EUVAC heating with Chapman depths, June solstice"),
+    "shell32x16_p2_comp": (lambda: shell_desc(n=32, nr=16, p=2, euvac=True, day=172.0, composition=True),
+                           "cubed-sphere shell 6x32x32x16, p=2, variable composition (O, N2, O2, He) with eddy "
+                           "transport and four-absorber EUVAC heating, June solstice"),
     "shell48x16_p3_euv": (lambda: shell_desc(n=48, nr=16, p=3, euv=True),
                           "cubed-sphere shell 6x48x48x16, p=3, EUV"),
 }

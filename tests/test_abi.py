@@ -47,3 +47,6 @@ def test_descriptor_roundtrip():
     c = DG.to_c_desc(d)
     assert c.p == 3 and c.nx == 4 and abs(c.grashof - d.grashof) < 1e-9 * d.grashof
     assert list(c.omega) == list(d.omega) and c.euv == 1
+    d2 = W.shell_desc(n=2, nr=2, p=1, euvac=True, composition=True)
+    c2 = DG.to_c_desc(d2)
+    assert c2.euv == 2 and c2.comp == 1 and list(c2.comp_b) == list(d2.comp_b) and c2.ref_T0 == d2.ref_T0
