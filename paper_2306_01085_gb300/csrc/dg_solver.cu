@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "dg_internal.cuh"
 
 namespace dg {
@@ -388,6 +390,141 @@ __global__ void k_scatter_col(long long E, int n, int j, double c, const double*
   }
 }
 
+// The same Gauss-Jordan inversion for blocks too large for one CTA's shared memory: one cluster of
+// CL CTAs per block, CTA `rank` keeping columns [rank w, rank w + w) (the last CTA fewer) resident in
+// its shared memory. At step k the CTA owning column k finds the pivot row p, and writes column k
+// with rows k and p interchanged, p and the reciprocal pivot into every CTA's buffer (distributed
+// shared memory, two buffers used in turn), then one cluster barrier; every CTA interchanges rows k
+// and p, scales row k and eliminates in its own columns exactly as the single-CTA kernel does. The
+// reverse column interchanges become each column's final position, where each CTA writes its
+// columns back. Cluster barriers at entry and exit keep every remote write inside the lifetime of
+// the CTA it targets. Each lane keeps its MR rows of the pivot column in registers for every
+// column it updates, and the pivot search reduces with warp shuffles.
+template <int MR, int NT>
+__global__ void __launch_bounds__(NT) k_gj_inverse_cluster(long long E, int n, int w, float* __restrict__ blocks,
+                                                            int* __restrict__ piv, int* __restrict__ info) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const long long e = blockIdx.x / CL;
+  extern __shared__ float sgj[];
+  float* A = sgj;                     // [w][n] own columns
+  float* pcol = A + (size_t)w * n;    // [2][n] pivot columns
+  float* r = pcol + 2 * n;            // [w] scaled row k of the own columns
+  int* pv = reinterpret_cast<int*>(r + w);
+  int* cur = pv + n;
+  int* dest = cur + n;
+  constexpr int NWARP = NT / 32;
+  __shared__ float wval[NWARP];
+  __shared__ int widx[NWARP];
+  __shared__ int spiv[2];
+  __shared__ float sinv[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j0 = rank * w;
+  const int nw = min(n, j0 + w) - j0;
+  float* Ag = blocks + e * (long long)n * n;
+  for (long long t = threadIdx.x; t < (long long)nw * n; t += blockDim.x) A[t] = Ag[(long long)j0 * n + t];
+  cl.sync();
+  for (int k = 0; k < n; ++k) {
+    const int b = k & 1;
+    if (k / w == rank) {
+      const float* col = A + (long long)(k - j0) * n;
+      float best = -1.0f;
+      int bi = k;
+      for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+        const float a = fabsf(col[i]);
+        if (a > best) { best = a; bi = i; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const float o = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
+      }
+      if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
+      __syncthreads();
+      if (warp == 0) {
+        best = lane < NWARP ? wval[lane] : -1.0f;
+        bi = lane < NWARP ? widx[lane] : n;
+        for (int off = 16; off > 0; off >>= 1) {
+          const float o = __shfl_down_sync(0xffffffffu, best, off);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
+        }
+        if (lane == 0) { wval[0] = best; widx[0] = bi; }
+      }
+      __syncthreads();
+      const int p = widx[0];
+      if (threadIdx.x == 0 && !(wval[0] > 0.0f)) atomicExch(info, 1);
+      const float pinv = 1.0f / col[p];
+      for (int q = 0; q < CL; ++q) {
+        float* dst = cl.map_shared_rank(pcol + b * n, q);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = (i == k) ? col[p] : (i == p ? col[k] : col[i]);
+        if (threadIdx.x == 0) {
+          *cl.map_shared_rank(spiv + b, q) = p;
+          *cl.map_shared_rank(sinv + b, q) = pinv;
+        }
+      }
+    }
+    cl.sync();
+    const int p = spiv[b];
+    const float pinv = sinv[b];
+    const float* f = pcol + b * n;
+    if (threadIdx.x == 0) pv[k] = p;
+    for (int jj = threadIdx.x; jj < nw; jj += blockDim.x) {
+      float* col = A + (long long)jj * n;
+      if (p != k) {
+        const float t = col[k];
+        col[k] = col[p];
+        col[p] = t;
+      }
+      r[jj] = (j0 + jj == k ? 1.0f : col[k]) * pinv;
+    }
+    // this lane's rows of the pivot column, in registers for every column it updates
+    float fr[MR];
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+      const int i = lane + 32 * m;
+      fr[m] = (i < n && i != k) ? f[i] : 0.0f;
+    }
+    __syncthreads();
+    for (int jj = warp; jj < nw; jj += NWARP) {
+      float* col = A + (long long)jj * n;
+      const float rj = r[jj];
+      const bool piv_col = (j0 + jj == k);
+      float v[MR];
+#pragma unroll
+      for (int m = 0; m < MR; ++m) {
+        const int i = lane + 32 * m;
+        v[m] = (i < n && !piv_col) ? col[i] : 0.0f;
+      }
+#pragma unroll
+      for (int m = 0; m < MR; ++m) {
+        const int i = lane + 32 * m;
+        if (i < n) col[i] = (i == k) ? rj : fmaf(-fr[m], rj, v[m]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) cur[i] = i;
+    for (int k = n - 1; k >= 0; --k) {
+      const int t = cur[k];
+      cur[k] = cur[pv[k]];
+      cur[pv[k]] = t;
+    }
+    for (int i = 0; i < n; ++i) dest[cur[i]] = i;
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nw; ++jj) {
+    float* out = Ag + (long long)dest[j0 + jj] * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = A[(long long)jj * n + i];
+  }
+  if (rank == 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) piv[e * n + i] = pv[i];
+  cl.sync();
+}
+
 // in-place Gauss-Jordan inversion with partial pivoting of one n x n column-major block per CTA
 // (A[j n + i] = row i, column j). Step k: pick the pivot row in column k, interchange it with row
 // k, scale row k by the reciprocal pivot (the pivot position takes the reciprocal itself) and
@@ -725,6 +862,43 @@ static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double 
   return DG_OK;
 }
 
+// the cluster Gauss-Jordan for blocks above one CTA's shared memory: the fewest CTAs (at most 8)
+// whose column slices fit 220 KB each; false (nothing launched) when no cluster fits
+static bool gj_cluster(dg_mesh* m, Solver* S, int n, cudaStream_t s) {
+  const long long budget = 220 * 1024 / 4;                      // floats per CTA
+  const long long wmax = (budget - 6LL * n) / (n + 1);
+  if (wmax < 1) return false;
+  const int CL = (int)((n + wmax - 1) / wmax);
+  if (CL < 2 || CL > 8) return false;
+  const int w = (n + CL - 1) / CL;
+  const size_t smem = sizeof(float) * ((size_t)w * n + 2 * n + w) + sizeof(int) * 3 * (size_t)n;
+  if (n > 640) return false;
+  constexpr int NT = 512;
+  auto kern = (n <= 320) ? k_gj_inverse_cluster<10, NT> : k_gj_inverse_cluster<20, NT>;   // rows per lane
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(m->E * CL));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, m->E, n, w, S->blocks, S->piv, S->info) == cudaSuccess;
+}
+
 static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, cudaStream_t s, bool f32 = false) {
   int rc = ensure_blocks(m, S);
   if (rc) return rc;
@@ -737,7 +911,7 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
   if (gj_smem <= 200 * 1024) {
     cudaFuncSetAttribute(k_gj_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem);
     k_gj_inverse<true><<<(unsigned)m->E, 256, gj_smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
-  } else {
+  } else if (!gj_cluster(m, S, nb, s)) {
     k_gj_inverse<false><<<(unsigned)m->E, 256, sizeof(float) * 2 * nb, s>>>(m->E, nb, S->blocks, S->piv, S->info);
   }
   prof_end(m, s);

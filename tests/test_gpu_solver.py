@@ -31,12 +31,15 @@ def test_dirk_tableau_matches_oracle(torch_cuda, stages):
     assert np.abs(a - A).max() < 1e-14 and np.abs(c - cc).max() < 1e-14
 
 
-def test_block_jacobi_solve_inverts_the_assembled_blocks(torch_cuda):
-    """dg_precond_apply (FP32 LU with partial pivoting) against an FP64 solve of the same blocks."""
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_block_jacobi_solve_inverts_the_assembled_blocks(torch_cuda, p):
+    """dg_precond_apply (FP32 Gauss-Jordan inverses) against an FP64 solve of the same blocks: one
+    CTA per block in shared memory at p = 2 (135^2), a cluster of CTAs sharing each block at p = 3
+    (320^2, 2 CTAs) and p = 4 (625^2, 8 CTAs)."""
     torch = torch_cuda
     from paper_2306_01085_gb300.dg import Mesh
-    d = W.shell_desc(n=2, nr=4, p=2, euv=True)
-    d.h_first = 0.0                      # uniform 125 km layers keep the interpolated T positive
+    d = W.shell_desc(n=2 if p == 2 else 1, nr=4 if p == 2 else 2, p=p, euv=True)
+    d.h_first = 0.0                      # uniform layers keep the interpolated T positive
     m = Mesh(d)
     u = torch.from_numpy(W.state_for(d, m.nodes().cpu().numpy(), 4)).cuda()
     c = 0.8
