@@ -392,6 +392,7 @@ def main_implicit(args):
     mixed_rb_bj: mixed precision, the reduced basis of the last 8 Newton updates (Sec. 3.2) over
                 block-Jacobi, with the RB initial guess
     mixed_rb:   mixed precision, the reduced basis over the mass matrix (nothing assembled)
+    mixed_bj16: mixed_bj with the inverses stored as FP16 (power-of-two column scales)
     Every variant starts from the same state; the final states are compared with plain_bj.
     """
     import numpy as np
@@ -415,6 +416,7 @@ def main_implicit(args):
     variants["mixed_mlp"] = dict(precond="mlp", jv_prec="f32")
     variants["mixed_rb_bj"] = dict(precond="rb_bj", jv_prec="f32")
     variants["mixed_rb"] = dict(precond="rb", jv_prec="f32")
+    variants["mixed_bj16"] = dict(precond="bj16", jv_prec="f32")
     results, finals = {}, {}
     training = None
     if "mixed_mlp" in args.variants.split(","):

@@ -235,6 +235,7 @@ int dg_residual_static(dg_mesh* mesh, const double* u, double t, double* r, void
 #define DG_PC_MLP  2         /* learned diagonal + low-rank inverse per element */
 #define DG_PC_RB   3         /* reduced basis of the last Newton updates over the mass matrix (Sec. 3.2) */
 #define DG_PC_RB_BJ 4        /* reduced basis over block-Jacobi */
+#define DG_PC_BJ16 5         /* block-Jacobi with the FP32 inverses stored as FP16, power-of-two scale per column */
 
 #define DG_REFRESH_STEP   0  /* build the preconditioner once per step, at u_n */
 #define DG_REFRESH_STAGE  1  /* rebuild at the start of every stage */
@@ -300,6 +301,10 @@ int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, const dg_sol
  * inverted in place in FP32 by Gauss-Jordan elimination with partial pivoting, so that applying
  * the preconditioner is one coalesced dense product per element. Synchronises the stream.
  * DG_ENAN on a zero pivot.
+ * DG_PC_BJ16: as DG_PC_BJ, then every column j of an inverse is divided by the power of two c_j
+ * just above its largest magnitude and rounded to FP16 (relative error 2^-11 per entry down to
+ * 2^-14 c_j); the apply streams half the bytes of DG_PC_BJ and sums in FP32. Extra storage:
+ * n_elem (5 n_p) ceil8(5 n_p) halves and n_elem 5 n_p floats.
  * The blocks are exact when no two faces of an element border the same neighbour (every shell;
  * boxes with at least 3 elements along each periodic direction); otherwise the gradient lifted
  * from one shared face into the other is left out and the block is an approximation.

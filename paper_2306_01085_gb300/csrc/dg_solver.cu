@@ -14,6 +14,7 @@
 #include <vector>
 
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 
 #include "dg_internal.cuh"
 
@@ -640,6 +641,76 @@ __global__ void k_inv_apply(long long E, int n, const float* __restrict__ inv, c
   }
 }
 
+// FP16 copy of the FP32 inverses (DG_PC_BJ16): column j of an element's inverse is stored as
+// B^{-1}[:, j] / c_j, c_j = 2^e the power of two just above the column's largest magnitude (the
+// division is exact, only the FP16 rounding remains: 2^-11 relative down to 2^-14 c_j, 2^-25 c_j
+// absolute below), in ld >= n halves with ld a multiple of 8 and zero padding rows. One warp per column.
+__global__ void k_inv_to_half(long long ncol, int n, int ld, const float* __restrict__ inv, __half* __restrict__ H,
+                              float* __restrict__ scale) {
+  const long long col = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= ncol) return;
+  const float* a = inv + col * n;
+  float mx = 0.0f;
+  for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(a[i]));
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  int ex = 0;
+  if (mx > 0.0f) frexpf(mx, &ex);          // mx = f 2^ex, f in [0.5, 1)
+  __half* h = H + col * ld;
+  for (int i = lane; i < ld; i += 32) h[i] = __float2half_rn(i < n ? ldexpf(a[i], -ex) : 0.0f);
+  if (lane == 0) scale[col] = ldexpf(1.0f, ex);
+}
+
+__device__ __forceinline__ void fma_half8(float* acc, const uint4& v, float xj) {
+  const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __half22float2(h[k]);
+    acc[2 * k] = fmaf(f.x, xj, acc[2 * k]);
+    acc[2 * k + 1] = fmaf(f.y, xj, acc[2 * k + 1]);
+  }
+}
+
+// y = B^{-1} x per element from the FP16 columns: y = sum_j H[:, j] (c_j x_j). Thread (rc, g) owns
+// rows 8 rc .. 8 rc + 7 (one 16-byte streaming load per column) and the columns j = g (mod G); the
+// G partial sums meet in shared memory. R = ld / 8 <= blockDim.x. x and y may alias.
+__global__ void __launch_bounds__(256) k_inv_apply_h(long long E, int n, int ld, const __half* __restrict__ H,
+                                                     const float* __restrict__ scale, const double* x, double* y) {
+  extern __shared__ float sh[];
+  const int R = ld >> 3;
+  const int G = blockDim.x / R;
+  float* sx = sh;            // [ld]
+  float* part = sh + ld;     // [G][ld]
+  const long long e = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sx[i] = scale[e * n + i] * (float)x[e * n + i];
+  __syncthreads();
+  const int rc = threadIdx.x % R, g = threadIdx.x / R;
+  if (g < G) {
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const uint4* Hc = reinterpret_cast<const uint4*>(H + e * (long long)n * ld) + rc;
+    int j = g;
+    for (; j + 3 * G < n; j += 4 * G) {
+      const uint4 v0 = __ldcs(Hc + (long long)j * R);
+      const uint4 v1 = __ldcs(Hc + (long long)(j + G) * R);
+      const uint4 v2 = __ldcs(Hc + (long long)(j + 2 * G) * R);
+      const uint4 v3 = __ldcs(Hc + (long long)(j + 3 * G) * R);
+      fma_half8(acc, v0, sx[j]);
+      fma_half8(acc, v1, sx[j + G]);
+      fma_half8(acc, v2, sx[j + 2 * G]);
+      fma_half8(acc, v3, sx[j + 3 * G]);
+    }
+    for (; j < n; j += G) fma_half8(acc, __ldcs(Hc + (long long)j * R), sx[j]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part[g * ld + 8 * rc + q] = acc[q];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float sum = 0.0f;
+    for (int k = 0; k < G; ++k) sum += part[k * ld + i];
+    y[e * n + i] = (double)sum;
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // solver storage
 // ------------------------------------------------------------------------------------------
@@ -656,6 +727,10 @@ struct Solver {
   int* piv = nullptr;
   int* info = nullptr;
   bool bj_ready = false;
+  __half* blocks_h = nullptr;  // [E][5Np][ld]: FP16 columns of the inverses (DG_PC_BJ16)
+  float* hscale = nullptr;     // [E][5Np]: their power-of-two column scales
+  int hld = 0;
+  bool bj16_ready = false;
   // reduced basis (Sec. 3.2): ring of the last Newton updates, orthonormal basis W, Z = J_G W,
   // Y = P0^{-1} Z - W, C = (W^T P0^{-1} Z)^{-1} on the device, Gram Z^T Z on the host
   int rb_cap = 0, rb_count = 0, rb_head = 0, rb_r = 0, rb_kind = 0;
@@ -675,7 +750,7 @@ enum { VU = 0, VKNOWN, VR0, VR1, VR2, VG, VRES, VZ, VW, VDU, VTMP, VUN };
 
 static void solver_free(Solver* S) {
   if (!S) return;
-  void* ptrs[] = {S->V, S->vec, S->partial, S->hdev, S->probe, S->blocks, S->piv, S->info,
+  void* ptrs[] = {S->V, S->vec, S->partial, S->hdev, S->probe, S->blocks, S->piv, S->info, S->blocks_h, S->hscale,
                   S->rb_ring, S->rb_W, S->rb_Z, S->rb_Y, S->rb_C, S->rb_s};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -899,10 +974,18 @@ static bool gj_cluster(dg_mesh* m, Solver* S, int n, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, kern, m->E, n, w, S->blocks, S->piv, S->info) == cudaSuccess;
 }
 
-static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, cudaStream_t s, bool f32 = false) {
+static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, cudaStream_t s, bool f32 = false,
+                    bool half = false) {
   int rc = ensure_blocks(m, S);
   if (rc) return rc;
   const int nb = 5 * m->np;
+  S->bj_ready = S->bj16_ready = false;
+  if (half && !S->blocks_h) {
+    S->hld = (nb + 7) / 8 * 8;
+    cudaError_t err = cudaMalloc(&S->blocks_h, sizeof(__half) * (size_t)m->E * nb * S->hld);
+    if (err == cudaSuccess) err = cudaMalloc(&S->hscale, sizeof(float) * (size_t)m->E * nb);
+    if (err != cudaSuccess) return fail(DG_ENOMEM, std::string("FP16 block storage: ") + cudaGetErrorString(err));
+  }
   DG_CUDA_TRY(cudaMemsetAsync(S->info, 0, sizeof(int), s));
   rc = bj_assemble(m, S, U, t, c, S->blocks, s, f32);
   if (rc) return rc;
@@ -921,6 +1004,14 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
   DG_CUDA_TRY(cudaStreamSynchronize(s));
   if (info) return fail(DG_ENAN, "block-Jacobi: a zero pivot in a diagonal block");
   S->bj_ready = true;
+  if (half) {
+    const long long ncol = m->E * (long long)nb;
+    prof_begin(m, s, KK_LU);
+    k_inv_to_half<<<(unsigned)((ncol + 7) / 8), 256, 0, s>>>(ncol, nb, S->hld, S->blocks, S->blocks_h, S->hscale);
+    prof_end(m, s);
+    DG_LAUNCH_CHECK("k_inv_to_half");
+    S->bj16_ready = true;
+  }
   return DG_OK;
 }
 
@@ -1116,6 +1207,18 @@ static int precond_apply(dg_mesh* m, Solver* S, int kind, const double* x, doubl
     DG_LAUNCH_CHECK("k_inv_apply");
     return DG_OK;
   }
+  if (kind == DG_PC_BJ16) {
+    if (!S->bj16_ready) return fail(DG_EINVAL, "FP16 block-Jacobi preconditioner used before dg_precond_setup");
+    const int nb = 5 * m->np, R = S->hld / 8;
+    if (R > 256) return fail(DG_EINVAL, "FP16 block-Jacobi: blocks larger than 2048");
+    const int G = 256 / R;
+    prof_begin(m, s, KK_PRECOND);
+    k_inv_apply_h<<<(unsigned)m->E, 256, sizeof(float) * (size_t)S->hld * (1 + G), s>>>(m->E, nb, S->hld,
+                                                                                      S->blocks_h, S->hscale, x, y);
+    prof_end(m, s);
+    DG_LAUNCH_CHECK("k_inv_apply_h");
+    return DG_OK;
+  }
   if (kind == DG_PC_MLP) {
     prof_begin(m, s, KK_PRECOND);
     const int rc = mlp_apply(m, x, y, s);
@@ -1179,6 +1282,7 @@ static int rb_build(dg_mesh* m, Solver* S, int kind, const double* U, double t, 
 // (re)build the preconditioner of kind at state U
 static int pc_setup(dg_mesh* m, Solver* S, int kind, const double* U, double t, double c, cudaStream_t s, bool f32) {
   if (kind == DG_PC_BJ || kind == DG_PC_RB_BJ) return bj_setup(m, S, U, t, c, s, f32);
+  if (kind == DG_PC_BJ16) return bj_setup(m, S, U, t, c, s, f32, true);
   if (kind == DG_PC_MLP) return mlp_setup(m, U, c, s);
   return DG_OK;
 }
@@ -1311,6 +1415,7 @@ extern "C" int dg_precond_setup(dg_mesh* mesh, int32_t kind, const double* u, do
   if (rc) return rc;
   if (kind == DG_PC_NONE) return DG_OK;
   if (kind == DG_PC_BJ) return bj_setup(mesh, S, u, t, dt_aii, (cudaStream_t)stream);
+  if (kind == DG_PC_BJ16) return bj_setup(mesh, S, u, t, dt_aii, (cudaStream_t)stream, false, true);
   if (kind == DG_PC_MLP) return mlp_setup(mesh, u, dt_aii, (cudaStream_t)stream);
   return fail(DG_EINVAL, "dg_precond_setup: unknown kind");
 }
@@ -1373,7 +1478,7 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
   int rc = dirk_tableau(o.stages, A, c);
   if (rc) return rc;
   if (o.max_newton < 1 || o.max_restarts < 1) return fail(DG_EINVAL, "dg_implicit_step: bad limits");
-  if (o.precond < DG_PC_NONE || o.precond > DG_PC_RB_BJ) return fail(DG_EINVAL, "dg_implicit_step: unknown precond");
+  if (o.precond < DG_PC_NONE || o.precond > DG_PC_BJ16) return fail(DG_EINVAL, "dg_implicit_step: unknown precond");
   const bool rb = o.precond == DG_PC_RB || o.precond == DG_PC_RB_BJ;
   Solver* S = nullptr;
   rc = solver_get(mesh, o.gmres_restart, &S);

@@ -58,7 +58,7 @@ class DgStepStats(ctypes.Structure):
     ]
 
 
-PC = {"none": 0, "bj": 1, "mlp": 2, "rb": 3, "rb_bj": 4}
+PC = {"none": 0, "bj": 1, "mlp": 2, "rb": 3, "rb_bj": 4, "bj16": 5}
 REFRESH = {"step": 0, "stage": 1, "newton": 2}
 
 _lib = None

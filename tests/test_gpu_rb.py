@@ -130,8 +130,8 @@ def test_rb_implicit_steps_match_oracle(torch_cuda, base):
 
 
 def test_rb_over_block_jacobi_on_a_stratified_shell(torch_cuda):
-    """DIRK(3,3) steps of 60 s on a stratified shell: block-Jacobi alone and the RB preconditioner
-    over block-Jacobi reach the same states within the Newton tolerance."""
+    """DIRK(3,3) steps of 60 s on a stratified shell: block-Jacobi alone, with FP16 inverses, and
+    the RB preconditioner over block-Jacobi reach the same states within the Newton tolerance."""
     torch = torch_cuda
     from paper_2306_01085_gb300.dg import Mesh
     d = W.shell_desc(n=3, nr=6, p=2, euv=True)
@@ -139,14 +139,14 @@ def test_rb_over_block_jacobi_on_a_stratified_shell(torch_cuda):
     u0 = torch.from_numpy(W.state_for(d, m.nodes().cpu().numpy(), 8)).cuda()
     dt = 60.0 / W.shell_reference().t0
     out = {}
-    for pc in ("bj", "rb_bj"):
+    for pc in ("bj", "rb_bj", "bj16"):
         u = u0.clone()
         m.rb_reset()
         sts = [m.implicit_step(u, k * dt, dt, stages=3, precond=pc) for k in range(2)]
         out[pc] = (sts, u.cpu().numpy())
     m.close()
     du = np.abs(out["bj"][1] - u0.cpu().numpy()).max(axis=(0, 2))
-    diff = np.abs(out["rb_bj"][1] - out["bj"][1]).max(axis=(0, 2))
-    print("\nGMRES per step  bj:", [sum(s["gmres"]) for s in out["bj"][0]],
-          " rb_bj:", [sum(s["gmres"]) for s in out["rb_bj"][0]])
-    assert np.all(diff <= 1e-4 * du), (diff, du)
+    print("\nGMRES per step", {pc: [sum(s["gmres"]) for s in out[pc][0]] for pc in out})
+    for pc in ("rb_bj", "bj16"):
+        diff = np.abs(out[pc][1] - out["bj"][1]).max(axis=(0, 2))
+        assert np.all(diff <= 1e-4 * du), (pc, diff, du)

@@ -54,6 +54,40 @@ def test_block_jacobi_solve_inverts_the_assembled_blocks(torch_cuda, p):
     assert err < 1e-6 * cond, (err, cond)
 
 
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_fp16_block_jacobi_is_the_fp32_inverse_rounded(torch_cuda, p):
+    """DG_PC_BJ16 against DG_PC_BJ on the same FP32 inverses A: every stored entry carries at most
+    2^-11 relative rounding (2^-25 c_j absolute in the subnormal range, c_j <= 2 max_i |A_ij|) and
+    both sums of n terms in FP32 err by at most n 2^-24 (|A| |x|)_i, so
+    |y16 - y32|_i <= (2^-11 + 2 n 2^-24) (|A| |x|)_i + 2^-24 sum_j max_i |A_ij| |x_j|,
+    with 10 % slack for taking |A| from an FP64 inverse of the assembled block."""
+    torch = torch_cuda
+    from paper_2306_01085_gb300.dg import Mesh
+    d = W.shell_desc(n=2 if p == 2 else 1, nr=4 if p == 2 else 2, p=p, euv=True)
+    d.h_first = 0.0
+    m = Mesh(d)
+    u = torch.from_numpy(W.state_for(d, m.nodes().cpu().numpy(), 4)).cuda()
+    c = 0.8
+    B = m.block_assemble(u, 0.2, c).cpu().numpy().astype(np.float64)
+    m.precond_setup("bj16", u, 0.2, c)
+    x = W.unit_vector(5, tuple(u.shape))
+    xg = torch.from_numpy(x).cuda()
+    y16 = m.precond_apply("bj16", xg).cpu().numpy().reshape(m.n_elem, -1)
+    y32 = m.precond_apply("bj", xg).cpu().numpy().reshape(m.n_elem, -1)
+    m.precond_setup("bj", u, 0.2, c)                   # rebuilding FP32 only retires the FP16 copy
+    with pytest.raises(Exception):
+        m.precond_apply("bj16", xg)
+    m.close()
+    Ainv = np.abs(np.linalg.inv(B))
+    xa = np.abs(x.reshape(m.n_elem, -1))
+    ax = np.einsum("eij,ej->ei", Ainv, xa)
+    cx = np.einsum("ej,ej->e", Ainv.max(axis=1), xa)[:, None]
+    n = B.shape[1]
+    bound = 1.1 * ((2.0 ** -11 + 2 * n * 2.0 ** -24) * ax + 2.0 ** -24 * cx)
+    assert np.all(np.abs(y16 - y32) <= bound), np.abs(y16 - y32).max() / ax.max()
+    assert np.abs(y16 - y32).max() > 0                 # the FP16 path is really a different path
+
+
 @pytest.mark.parametrize("case", ["box_p1", "shell_p2"])
 def test_block_assembly_matches_oracle_blocks(torch_cuda, case):
     """Assembled FP32 blocks against the oracle's FP64 brute-force blocks, entry by entry."""
