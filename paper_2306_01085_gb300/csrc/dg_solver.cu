@@ -328,6 +328,132 @@ __global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot_k(long long n2, c
   }
 }
 
+// FP32 Gram-Schmidt arithmetic on the FP64 basis (the mixed-precision solve, whose Jv is itself
+// FP32). On this GPU a cvt between FP64 and FP32 issues on the FP64 pipe, as slowly as a DFMA, so
+// the conversions are done on the integer pipe from the IEEE-754 bit layouts: to_f32 truncates the
+// significand to 24 bits (relative error below 2^-23) and flushes magnitudes under 2^-126 to zero;
+// to_f64 is exact for normal floats and flushes subnormal ones.
+__device__ __forceinline__ float to_f32(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned ef = e < 897u ? 0u : (e > 1150u ? 254u : e - 896u);
+  const unsigned m = ef ? (((hi & 0xfffffu) << 3) | (lo >> 29)) : 0u;
+  return __uint_as_float((hi & 0x80000000u) | (ef << 23) | m);
+}
+
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned hi = (b & 0x80000000u) | (e ? ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3) : 0u);
+  return __hiloint2double((int)hi, (int)(e ? b << 29 : 0u));
+}
+
+// k_mdot_k with FP32 products and per-thread FP32 sums (cross-thread sums in FP64); the |w|^2 row
+// stays FP64.
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS, 2) k_mdot_f32(long long n2, const double2* __restrict__ V, long long ldv2,
+                                                         const double2* __restrict__ w, double* __restrict__ partial) {
+  float acc[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j] = 0.0f;
+  double nrm = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double2 x = w[i];
+    const float xx = to_f32(x.x), xy = to_f32(x.y);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const double2 v = V[j * ldv2 + i];
+      acc[j] = fmaf(to_f32(v.x), xx, fmaf(to_f32(v.y), xy, acc[j]));
+    }
+    nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+  }
+  __shared__ double red[RED_THREADS / 32][K + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    double v = to_f64(acc[j]);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][j] = v;
+  }
+  for (int off = 16; off > 0; off >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, off);
+  if (lane == 0) red[warp][K] = nrm;
+  __syncthreads();
+  for (int j = threadIdx.x; j <= K; j += blockDim.x) {
+    double v = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) v += red[q][j];
+    partial[j * RED_BLOCKS + blockIdx.x] = v;
+  }
+}
+
+// k_update_dot_k with the correction sum_j h_j V_j formed in FP32 and subtracted from w in FP64
+// (one FP64 add per entry), the element's truncated V values kept in registers for the FP32
+// dots; |w|^2 in FP64. Partial rows as k_update_dot_k.
+template <int K, bool DOTS>
+__global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot_f32(long long n2, const double2* __restrict__ V,
+                                                                  long long ldv2, const double* __restrict__ h,
+                                                                  double2* __restrict__ w, double* __restrict__ partial) {
+  __shared__ float hs[K];
+  if (threadIdx.x < K) hs[threadIdx.x] = to_f32(h[threadIdx.x]);
+  __syncthreads();
+  constexpr int NA = DOTS ? K : 1;
+  constexpr bool CACHE = DOTS && K <= 24;   // the truncated V values stay in registers for the dots
+  float acc[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) acc[j] = 0.0f;
+  double nrm = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    double2 x = w[i];
+    float2 vf[CACHE ? K : 1];
+    float cx = 0.0f, cy = 0.0f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const double2 v = V[j * ldv2 + i];
+      const float2 f = make_float2(to_f32(v.x), to_f32(v.y));
+      if constexpr (CACHE) vf[j] = f;
+      cx = fmaf(hs[j], f.x, cx);
+      cy = fmaf(hs[j], f.y, cy);
+    }
+    x.x -= to_f64(cx);
+    x.y -= to_f64(cy);
+    w[i] = x;
+    if constexpr (DOTS) {
+      const float xx = to_f32(x.x), xy = to_f32(x.y);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        float2 f;
+        if constexpr (CACHE) {
+          f = vf[j];
+        } else {   // the element was just read: an L2 hit
+          const double2 v = __ldcg(&V[j * ldv2 + i]);
+          f = make_float2(to_f32(v.x), to_f32(v.y));
+        }
+        acc[j] = fmaf(f.x, xx, fmaf(f.y, xy, acc[j]));
+      }
+    }
+    nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+  }
+  __shared__ double red[RED_THREADS / 32][NA + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if constexpr (DOTS) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      double a = to_f64(acc[j]);
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+      if (lane == 0) red[warp][j] = a;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, off);
+  if (lane == 0) red[warp][NA] = nrm;
+  __syncthreads();
+  // DOTS: rows 0..K-1 the dots, row K |w|^2; otherwise row 0 |w|^2
+  for (int j = threadIdx.x; j < (DOTS ? K + 1 : 1); j += blockDim.x) {
+    const int src = DOTS ? j : NA;
+    double a = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) a += red[q][src];
+    partial[j * RED_BLOCKS + blockIdx.x] = a;
+  }
+}
+
 // out[j] = sum_b partial[j][b] (+= into out when accumulate); also out_sq = partial[k] sum
 __global__ void k_mdot_finish(int k, const double* __restrict__ partial, double* __restrict__ out, int accumulate) {
   const int j = threadIdx.x;
@@ -821,9 +947,24 @@ static unsigned grid_for(long long n) {
 #define DG_K_CASES(X)                                                                                   \
   X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18)    \
   X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
+#define DG_K_CASES1(X)                                                                                  \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18)         \
+  X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
 
 // partial rows 0..k-1 = V^T w, row k = |w|^2 (k vectors of length n, leading dimension n)
-static void mdot(long long n, int k, const double* V, const double* w, double* partial, cudaStream_t s) {
+static void mdot(long long n, int k, const double* V, const double* w, double* partial, cudaStream_t s,
+                 bool f32 = false) {
+  if (f32 && n % 2 == 0 && k >= 1 && k <= 32) {
+    const long long n2 = n / 2;
+    const double2* V2 = reinterpret_cast<const double2*>(V);
+    const double2* w2 = reinterpret_cast<const double2*>(w);
+    switch (k) {
+#define DG_MDF(K) \
+  case K: k_mdot_f32<K><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V2, n2, w2, partial); return;
+      DG_K_CASES1(DG_MDF)
+#undef DG_MDF
+    }
+  }
   if (n % 2 == 0 && k <= 32) {
     const long long n2 = n / 2;
     const double2* V2 = reinterpret_cast<const double2*>(V);
@@ -840,7 +981,21 @@ static void mdot(long long n, int k, const double* V, const double* w, double* p
 
 // w <- w - V h (k vectors); partial rows: DOTS ? (V^T w, |w|^2 at row k) : |w|^2 at row 0
 static void update_dot(long long n, int k, const double* V, const double* h, double* w, double* partial, bool dots,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool f32 = false) {
+  if (f32 && n % 2 == 0 && k >= 1 && k <= 32) {
+    const long long n2 = n / 2;
+    const double2* V2 = reinterpret_cast<const double2*>(V);
+    double2* w2 = reinterpret_cast<double2*>(w);
+    switch (k) {
+#define DG_UDF(K)                                                                                 \
+  case K:                                                                                         \
+    if (dots) k_update_dot_f32<K, true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V2, n2, h, w2, partial);  \
+    else k_update_dot_f32<K, false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V2, n2, h, w2, partial);      \
+    return;
+      DG_K_CASES1(DG_UDF)
+#undef DG_UDF
+    }
+  }
   if (n % 2 == 0 && k >= 1 && k <= 32) {
     const long long n2 = n / 2;
     const double2* V2 = reinterpret_cast<const double2*>(V);
@@ -1306,6 +1461,7 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
   if (!x0_given || bnorm == 0.0) DG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   if (bnorm == 0.0) return DG_OK;
   std::vector<double> H((size_t)(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
+  const bool f32gs = o.jv_prec == DG_PREC_F32;
   for (int cycle = 0; cycle < o.max_restarts; ++cycle) {
     // r = b - A x
     if (cycle == 0) {
@@ -1332,14 +1488,16 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
       if (rc) return rc;
       rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, z, w, s);
       if (rc) return rc;
-      // classical Gram-Schmidt twice; h and the norm stay on the device until one read-back
+      // classical Gram-Schmidt twice; h and the norm stay on the device until one read-back. With
+      // the FP32 Jv the projections are formed in FP32 arithmetic (orthogonality to ~1e-7, far
+      // below the Krylov tolerance), the basis, the subtraction from w and the norms stay FP64.
       prof_begin(m, s, KK_BLAS);
       // h1 = V^T w; w -= V h1 fused with h2 = V^T w; w -= V h2 fused with |w|^2
-      mdot(n, k + 1, V, w, S->partial, s);
+      mdot(n, k + 1, V, w, S->partial, s, f32gs);
       k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev, 0);
-      update_dot(n, k + 1, V, S->hdev, w, S->partial, true, s);
+      update_dot(n, k + 1, V, S->hdev, w, S->partial, true, s, f32gs);
       k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev + MAXK, 0);
-      update_dot(n, k + 1, V, S->hdev + MAXK, w, S->partial, false, s);
+      update_dot(n, k + 1, V, S->hdev + MAXK, w, S->partial, false, s, f32gs);
       k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev + MAXK + k + 1, 0);
       k_scale_dev<<<grid_for(n), 256, 0, s>>>(n, w, S->hdev + MAXK + k + 1, V + (long long)(k + 1) * n);
       prof_end(m, s);
