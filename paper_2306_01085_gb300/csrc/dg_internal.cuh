@@ -179,7 +179,7 @@ struct Driver {
                       bool tangent, cudaStream_t s, bool f32 = false, double stage_c = 0.0);
   static int q_to_nodal(dg_mesh* m, double* q, cudaStream_t s);
   static int q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s);
-  static int mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
+  static int mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s, bool f32 = false);
   static int mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s);
   static int mixture(dg_mesh* m);
   // J_r probe restricted to each element's own diagonal block (exact, one column per element)

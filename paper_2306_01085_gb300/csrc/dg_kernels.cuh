@@ -726,40 +726,41 @@ k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
 // tensor transforms of nodal q and the mass matrix
 // --------------------------------------------------------------------------------------------
 // out = A x A x A in (T: A^T) for C components of EPB elements per CTA (one thread per point of
-// each element), optional W-weighting and back-transform (mass matrix), optional face traces
-template <int N, bool T, int C>
+// each element), optional W-weighting and back-transform (mass matrix), optional face traces.
+// Arithmetic in R (FP32 for the mass columns of FP32-assembled blocks); input and output FP64.
+template <int N, bool T, int C, typename R = double>
 __global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, const double* __restrict__ in_g,
-                         double* __restrict__ out_g, const double* __restrict__ weight,
+                         double* __restrict__ out_g, const R* __restrict__ weight,
                          double* __restrict__ traces) {
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, EPB = Epb<N, 1>::value;
-  __shared__ SmemOps so;
-  extern __shared__ double smem[];
-  double* b0 = smem;                 // [EPB][C][NP]
-  double* b1 = smem + EPB * C * NP;  // [EPB][C][NP]
-  load_ops<N, double>(ops, so);
+  __shared__ SmemOpsT<R> so;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* b0 = reinterpret_cast<R*>(smem_raw);   // [EPB][C][NP]
+  R* b1 = b0 + EPB * C * NP;                // [EPB][C][NP]
+  load_ops<N, R>(ops, so);
   const long long e0 = (long long)blockIdx.x * EPB;
   for (int idx = threadIdx.x; idx < EPB * C * NP; idx += blockDim.x) {
     const long long e = e0 + idx / (C * NP);
-    if (e < E) b0[idx] = in_g[e0 * C * NP + idx];
+    if (e < E) b0[idx] = (R)in_g[e0 * C * NP + idx];
   }
   __syncthreads();
   const int el = threadIdx.x / NP, g = threadIdx.x % NP;
   const bool active = el < EPB && (e0 + el) < E;
-  const double* A = (which == 0) ? so.B : so.Binv;
-  double* in = b0;
-  double* out = b1;
+  const R* A = (which == 0) ? so.B : so.Binv;
+  R* in = b0;
+  R* out = b1;
   for (int dir = 0; dir < 3; ++dir) {
     if (active)
       for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, T>(A, in + (el * C + c) * NP, g, dir);
     __syncthreads();
-    double* tt = in;
+    R* tt = in;
     in = out;
     out = tt;
   }
   if (weight) {
     // mass matrix: W-weighted Gauss values, then back with B^T
     if (active) {
-      const double wd = weight[(e0 + el) * 10 * NP + 9 * NP + g];
+      const R wd = weight[(e0 + el) * 10 * NP + 9 * NP + g];
       for (int c = 0; c < C; ++c) in[(el * C + c) * NP + g] *= wd;
     }
     __syncthreads();
@@ -767,14 +768,14 @@ __global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, co
       if (active)
         for (int c = 0; c < C; ++c) out[(el * C + c) * NP + g] = line<N, true>(A, in + (el * C + c) * NP, g, dir);
       __syncthreads();
-      double* tt = in;
+      R* tt = in;
       in = out;
       out = tt;
     }
   }
   for (int idx = threadIdx.x; idx < EPB * C * NP; idx += blockDim.x) {
     const long long e = e0 + idx / (C * NP);
-    if (e < E) out_g[e0 * C * NP + idx] = in[idx];
+    if (e < E) out_g[e0 * C * NP + idx] = (double)in[idx];
   }
   if (traces) {
     for (int idx = threadIdx.x; idx < EPB * 6 * C * NF; idx += blockDim.x) {
@@ -782,10 +783,10 @@ __global__ void k_tensor(long long E, const Ops* __restrict__ ops, int which, co
       const long long e = e0 + l;
       if (e >= E) continue;
       const int phi = rem / (C * NF), c = (rem / NF) % C, f = rem % NF;
-      const double* ev = (phi & 1) ? so.eR : so.eL;
-      double acc = 0.0;
+      const R* ev = (phi & 1) ? so.eR : so.eL;
+      R acc = R(0);
       for (int k = 0; k < N; ++k) acc = fma(ev[k], in[(l * C + c) * NP + face_vol_point<N>(phi, f, k)], acc);
-      traces[e * 6 * C * NF + rem] = acc;
+      traces[e * 6 * C * NF + rem] = (double)acc;
     }
   }
 }
@@ -1196,10 +1197,10 @@ int Driver<N>::q_to_nodal(dg_mesh* m, double* q, cudaStream_t s) {
   constexpr int NP = Shape<N>::NP;
   constexpr int EPB = Epb<N, 1>::value;
   const size_t sm = sizeof(double) * 2 * EPB * 15 * NP;
-  int rc = set_smem(k_tensor<N, false, 15>, sm);
+  int rc = set_smem(k_tensor<N, false, 15, double>, sm);
   if (rc) return rc;
   prof_begin(m, s, KK_TENSOR);
-  k_tensor<N, false, 15><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, 1, m->ws.qg, q,
+  k_tensor<N, false, 15, double><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, 1, m->ws.qg, q,
                                                                                    nullptr, nullptr);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_tensor(q nodal)");
@@ -1211,10 +1212,10 @@ int Driver<N>::q_from_nodal(dg_mesh* m, const double* q, cudaStream_t s) {
   constexpr int NP = Shape<N>::NP;
   constexpr int EPB = Epb<N, 1>::value;
   const size_t sm = sizeof(double) * 2 * EPB * 15 * NP;
-  int rc = set_smem(k_tensor<N, false, 15>, sm);
+  int rc = set_smem(k_tensor<N, false, 15, double>, sm);
   if (rc) return rc;
   prof_begin(m, s, KK_TENSOR);
-  k_tensor<N, false, 15><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, 0, q, m->ws.qg,
+  k_tensor<N, false, 15, double><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, 0, q, m->ws.qg,
                                                                                    nullptr, m->ws.qf);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_tensor(q gauss)");
@@ -1243,15 +1244,25 @@ int Driver<N>::mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s)
 }
 
 template <int N>
-int Driver<N>::mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s) {
+int Driver<N>::mass(dg_mesh* m, const double* v, double* mv, cudaStream_t s, bool f32) {
   constexpr int NP = Shape<N>::NP;
   constexpr int EPB = Epb<N, 1>::value;
-  const size_t sm = sizeof(double) * 2 * EPB * 5 * NP;
-  int rc = set_smem(k_tensor<N, false, 5>, sm);
-  if (rc) return rc;
-  prof_begin(m, s, KK_TENSOR);
-  k_tensor<N, false, 5><<<(unsigned)((m->E + EPB - 1) / EPB), EPB * NP, sm, s>>>(m->E, m->d_ops, 0, v, mv, m->geo,
-                                                                                  nullptr);
+  const unsigned grid = (unsigned)((m->E + EPB - 1) / EPB);
+  int rc;
+  if (f32) {   // FP32 arithmetic on the FP32 geometry (ensure_f32 has run)
+    if (!m->w32.geo) return fail(DG_EINVAL, "FP32 mass apply without the FP32 geometry");
+    const size_t sm = sizeof(float) * 2 * EPB * 5 * NP;
+    rc = set_smem(k_tensor<N, false, 5, float>, sm);
+    if (rc) return rc;
+    prof_begin(m, s, KK_TENSOR);
+    k_tensor<N, false, 5, float><<<grid, EPB * NP, sm, s>>>(m->E, m->d_ops, 0, v, mv, m->w32.geo, nullptr);
+  } else {
+    const size_t sm = sizeof(double) * 2 * EPB * 5 * NP;
+    rc = set_smem(k_tensor<N, false, 5, double>, sm);
+    if (rc) return rc;
+    prof_begin(m, s, KK_TENSOR);
+    k_tensor<N, false, 5, double><<<grid, EPB * NP, sm, s>>>(m->E, m->d_ops, 0, v, mv, m->geo, nullptr);
+  }
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_tensor(mass)");
   return DG_OK;

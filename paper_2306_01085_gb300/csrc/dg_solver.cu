@@ -1082,7 +1082,7 @@ static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double 
     prof_end(m, s);
     DG_DISPATCH_S(m, jv_blockdiag(m, U, S->probe, t, jv, s, f32));
     if (rc) return rc;
-    rc = dg_mass_apply(m, S->probe, mv, s);
+    DG_DISPATCH_S(m, mass(m, S->probe, mv, s, f32));   // FP32 arithmetic for FP32 blocks
     if (rc) return rc;
     prof_begin(m, s, KK_BLAS);
     k_scatter_col<<<grid_for(S->n), 256, 0, s>>>(m->E, nb, j, c, mv, jv, dest);
