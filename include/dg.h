@@ -259,8 +259,12 @@ typedef struct dg_solver_opts {
     double gmres_rtol;       /* each Newton system to ||b - J x|| <= gmres_rtol ||b|| (1e-3) */
     double abs_floor;        /* or when ||G||_2 <= abs_floor ||M U||_2 (1e-14) */
     int32_t rb_size;         /* DG_PC_RB*: Newton updates kept in the reduced basis, 1..16 (8) */
-    int32_t reserved;        /* zero */
+    int32_t flags;           /* DG_OPT_* bits (0) */
 } dg_solver_opts;
+
+/* dg_solver_opts.flags: recompute the state's Gauss values, traces and LDG gradient in every
+ * operator application instead of once per Krylov solve (same results; for checking). */
+#define DG_OPT_RECOMPUTE_VALUE 1
 
 typedef struct dg_step_stats {
     int32_t status;                 /* the call's return code */

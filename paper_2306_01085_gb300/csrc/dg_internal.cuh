@@ -141,9 +141,13 @@ namespace dg {
 int ensure_f32(dg_mesh* m);       // allocate and fill the FP32 workspace and geometry
 }
 int mlp_setup(dg_mesh* mesh, const double* u, double dt_aii, cudaStream_t s);
-// J_G v = M v - c J_r(u) v in one tangent pass (exact tangent; FP32 arithmetic when f32)
+// J_G v = M v - c J_r(u) v in one tangent pass (exact tangent; FP32 arithmetic when f32). With
+// value_ready the workspace's value plane (Gauss values, traces and LDG gradient of u) was formed
+// by stage_value_plane for this u and nothing has overwritten it since: only v's tangent is
+// interpolated and differentiated.
 int stage_jvp(dg_mesh* mesh, const double* u, const double* v, double t, double c, double* out, bool f32,
-              cudaStream_t s);
+              cudaStream_t s, bool value_ready = false);
+int stage_value_plane(dg_mesh* mesh, const double* u, bool f32, cudaStream_t s);
 int mlp_apply(dg_mesh* mesh, const double* x, double* y, cudaStream_t s);
 
 void dg_solver_release(dg_mesh* m);
@@ -174,7 +178,8 @@ template <int N>
 struct Driver {
   static int geometry(dg_mesh* m, cudaStream_t s);
   // f32: FP32 data and arithmetic; inputs and outputs stay FP64
-  static int gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32 = false);
+  static int gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32 = false,
+                      bool tangent_only = false);
   static int residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
                       bool tangent, cudaStream_t s, bool f32 = false, double stage_c = 0.0);
   static int q_to_nodal(dg_mesh* m, double* q, cudaStream_t s);
@@ -190,7 +195,8 @@ struct Driver {
                      cudaStream_t s);
   template <int CM>
   static int eval_cm_t(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv, cudaStream_t s);
-  template <typename R> static int gradient_p(dg_mesh* m, const double* u, const double* v, cudaStream_t s);
+  template <typename R>
+  static int gradient_p(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool tangent_only);
   template <typename R>
   static int residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s, double stage_c);
   template <typename R>

@@ -222,12 +222,17 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
 // (u_hat picks up half of the own trace on interior faces) and qx receives, per face, the trace of
 // the gradient tangent this element would get from its neighbour's perturbation across that face:
 // kappa(f) (w n dS)(f) u_dot_nb(f) / 2 with kappa(f) = sum_k e_face[k]^2 / (w |J|)(g(f, k)).
-template <int N, int NC, bool BLK, typename R, int CM = CM_NATIVE>
+// TO (tangent only, NC = 1): the value plane of ug, uf, qg, qf already holds the state's values
+// (computed once for all the Jv of one Krylov solve); only the tangent plane is formed, with the
+// same arithmetic as the tangent of NC = 2, so the result is identical. The wall trace of the
+// tangent reads the value plane's varrho trace.
+template <int N, int NC, bool BLK, typename R, int CM = CM_NATIVE, bool TO = false>
 __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, const R* __restrict__ geo,
                        const R* __restrict__ fgeo, const int* __restrict__ nbr,
                        const int* __restrict__ nbr_fo, const R* __restrict__ ug,
                        const R* __restrict__ uf, R* __restrict__ qg, R* __restrict__ qf,
                        R* __restrict__ qx) {
+  static_assert(!TO || (NC == 1 && !BLK), "tangent-only gradient works on one plane");
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
   __shared__ SmemOpsT<R> so;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -241,11 +246,12 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
   load_ops<N, R>(ops, so);
   const long long e0 = (long long)blockIdx.x * EPB;
   const long long plane_g = E * 5 * NP, plane_f = E * 30 * NF;
+  const long long og = TO ? plane_g : 0, of = TO ? plane_f : 0;   // TO: read the tangent plane
   for (int idx = threadIdx.x; idx < EPB * 5 * NP; idx += blockDim.x) {
     const int l = idx / (5 * NP), rem = idx % (5 * NP);
     const long long e = e0 + l;
     if (e < E)
-      for (int pl = 0; pl < NC; ++pl) sU[(l * C + 5 * pl) * NP + rem] = ug[pl * plane_g + e * 5 * NP + rem];
+      for (int pl = 0; pl < NC; ++pl) sU[(l * C + 5 * pl) * NP + rem] = ug[og + pl * plane_g + e * 5 * NP + rem];
   }
   // traces: u_hat on every face point (Eq. LDG2), and the face geometry
   for (int idx = threadIdx.x; idx < EPB * 6 * NF; idx += blockDim.x) {
@@ -257,14 +263,14 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
     const int nb = nbr[e * 6 + phi];
     R own[10], oth[10];
     for (int pl = 0; pl < NC; ++pl)
-      for (int c = 0; c < 5; ++c) own[5 * pl + c] = uf[pl * plane_f + fbase + c * NF];
+      for (int c = 0; c < 5; ++c) own[5 * pl + c] = uf[of + pl * plane_f + fbase + c * NF];
     R* dst = sUh + ((l * 6 + phi) * C) * NF + f;
     if (nb >= 0) {
       const int fo = nbr_fo[e * 6 + phi];
       const int f2 = orient_map(fo >> 3, f % N, f / N, N);
       const long long nbase = (long long)nb * 30 * NF + (fo & 7) * 5 * NF + f2;
       for (int pl = 0; pl < NC; ++pl)
-        for (int c = 0; c < 5; ++c) oth[5 * pl + c] = uf[pl * plane_f + nbase + c * NF];
+        for (int c = 0; c < 5; ++c) oth[5 * pl + c] = uf[of + pl * plane_f + nbase + c * NF];
       if constexpr (BLK) {
         for (int c = 0; c < 5; ++c) {
           dst[c * NF] = R(0.5) * (own[c] + oth[c]);
@@ -285,6 +291,15 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
       if constexpr (BLK) {
         R* xo = qx + (e * 6 + phi) * 15 * NF + f;
         for (int k = 0; k < 15; ++k) xo[k * NF] = R(0);
+      }
+      if constexpr (TO) {
+        const R sr = s_exp(R(0.5) * uf[fbase]);   // value plane's varrho trace
+        dst[0] = own[0];
+        dst[NF] = R(0);
+        dst[2 * NF] = R(0);
+        dst[3 * NF] = R(0);
+        dst[4 * NF] = R(0.5) * sr * P.t_wall * own[0];
+        continue;
       }
       const R sr = s_exp(R(0.5) * own[0]);
       dst[0] = own[0];
@@ -354,7 +369,7 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
     const long long e = e0 + l;
     if (e < E)
       for (int pl = 0; pl < NC; ++pl)
-        qg[pl * E * 15 * NP + e * 15 * NP + rem] = sQ[((l * 3 + d) * C + 5 * pl + c) * NP + gg];
+        qg[(TO ? E * 15 * NP : 0) + pl * E * 15 * NP + e * 15 * NP + rem] = sQ[((l * 3 + d) * C + 5 * pl + c) * NP + gg];
   }
   for (int idx = threadIdx.x; idx < EPB * 6 * 15 * NF; idx += blockDim.x) {
     const int l = idx / (90 * NF), rem = idx % (90 * NF);
@@ -368,7 +383,7 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
       R acc = R(0);
 #pragma unroll
       for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
-      qf[pl * E * 90 * NF + e * 90 * NF + rem] = acc;
+      qf[(TO ? E * 90 * NF : 0) + pl * E * 90 * NF + e * 90 * NF + rem] = acc;
     }
   }
 }
@@ -1052,19 +1067,36 @@ static int run_interp(dg_mesh* m, const double* u, const double* v, cudaStream_t
   return DG_OK;
 }
 
-template <int N, int NC, bool BLK = false, typename R = double, int CM = CM_NATIVE>
+template <int N, int NC, bool BLK = false, typename R = double, int CM = CM_NATIVE, bool TO = false>
 static int run_grad(dg_mesh* m, cudaStream_t s) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
   const size_t sm = Smem<N, NC, R>::grad;
-  int rc = set_smem(k_grad<N, NC, BLK, R, CM>, sm);
+  int rc = set_smem(k_grad<N, NC, BLK, R, CM, TO>, sm);
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
   const WorkT<R> w = work_of<R>(m);
   prof_begin(m, s, KK_GRAD);
-  k_grad<N, NC, BLK, R, CM><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), w.geo, w.fgeo, m->nbr,
-                                                      m->nbr_fo, w.ug, w.uf, w.qg, w.qf, w.qx);
+  k_grad<N, NC, BLK, R, CM, TO><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), w.geo, w.fgeo,
+                                                          m->nbr, m->nbr_fo, w.ug, w.uf, w.qg, w.qf, w.qx);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_grad");
+  return DG_OK;
+}
+
+// the tangent plane of ug, uf (nodal v -> Gauss values and traces), with the NC = 1 kernel
+template <int N, typename R>
+static int run_interp_tangent(dg_mesh* m, const double* v, cudaStream_t s) {
+  constexpr int EPB = Epb<N, 1>::value, NP = Shape<N>::NP, NF = Shape<N>::NF;
+  const size_t sm = Smem<N, 1, R>::interp;
+  int rc = set_smem(k_interp<N, 1, R, CM_NATIVE>, sm);
+  if (rc) return rc;
+  const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
+  const WorkT<R> w = work_of<R>(m);
+  prof_begin(m, s, KK_INTERP);
+  k_interp<N, 1, R, CM_NATIVE><<<blocks, EPB * NP, sm, s>>>(v, nullptr, m->E, m->d_ops, w.ug + m->E * 5 * NP,
+                                                             w.uf + m->E * 30 * NF);
+  prof_end(m, s);
+  DG_LAUNCH_CHECK("k_interp(tangent)");
   return DG_OK;
 }
 
@@ -1117,7 +1149,12 @@ int Driver<N>::geometry(dg_mesh* m, cudaStream_t s) {
 
 template <int N>
 template <typename R>
-int Driver<N>::gradient_p(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
+int Driver<N>::gradient_p(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool tangent_only) {
+  if (tangent_only) {   // u's value plane is in place: the tangent of v alone
+    int rc = run_interp_tangent<N, R>(m, v, s);
+    if (rc) return rc;
+    return run_grad<N, 1, false, R, CM_NATIVE, true>(m, s);
+  }
   int rc = v ? run_interp<N, 2, R>(m, u, v, s) : run_interp<N, 1, R>(m, u, nullptr, s);
   if (rc) return rc;
   return v ? run_grad<N, 2, false, R>(m, s) : run_grad<N, 1, false, R>(m, s);
@@ -1133,8 +1170,8 @@ int Driver<N>::residual_p(dg_mesh* m, double t, double* r, double* jv, bool tang
 }
 
 template <int N>
-int Driver<N>::gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32) {
-  return f32 ? gradient_p<float>(m, u, v, s) : gradient_p<double>(m, u, v, s);
+int Driver<N>::gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32, bool tangent_only) {
+  return f32 ? gradient_p<float>(m, u, v, s, tangent_only) : gradient_p<double>(m, u, v, s, tangent_only);
 }
 
 template <int N>

@@ -31,8 +31,9 @@ int fail(int code, const std::string& msg) {
   }
 
 static int drv_geometry(dg_mesh* m, cudaStream_t s) { DG_DISPATCH(m, geometry(m, s)); }
-static int drv_gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32 = false) {
-  DG_DISPATCH(m, gradient(m, u, v, s, f32));
+static int drv_gradient(dg_mesh* m, const double* u, const double* v, cudaStream_t s, bool f32 = false,
+                        bool tangent_only = false) {
+  DG_DISPATCH(m, gradient(m, u, v, s, f32, tangent_only));
 }
 static int drv_residual(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv,
                         bool tan, cudaStream_t s, bool f32 = false, double stage_c = 0.0) {
@@ -746,15 +747,23 @@ extern "C" int dg_jvp_f32(dg_mesh* mesh, const double* u, const double* v, doubl
 }
 
 int stage_jvp(dg_mesh* mesh, const double* u, const double* v, double t, double c, double* out, bool f32,
-              cudaStream_t s) {
+              cudaStream_t s, bool value_ready) {
   if (c == 0.0) return fail(DG_EINVAL, "stage operator needs dt a_ii != 0");
   if (f32) {
     int rc = ensure_f32(mesh);
     if (rc) return rc;
   }
-  int rc = drv_gradient(mesh, u, v, s, f32);
+  int rc = drv_gradient(mesh, u, v, s, f32, value_ready);
   if (rc) return rc;
   return drv_residual(mesh, u, v, t, nullptr, out, true, s, f32, c);
+}
+
+int stage_value_plane(dg_mesh* mesh, const double* u, bool f32, cudaStream_t s) {
+  if (f32) {
+    int rc = ensure_f32(mesh);
+    if (rc) return rc;
+  }
+  return drv_gradient(mesh, u, nullptr, s, f32);
 }
 
 extern "C" int dg_eval_precision(dg_mesh* mesh, int32_t mode, const double* u, const double* v, double t, double* r,

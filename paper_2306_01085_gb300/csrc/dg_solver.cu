@@ -1032,9 +1032,9 @@ static void update_dot(long long n, int k, const double* V, const double* h, dou
 
 // J_G v = M v - c J_r(U) v
 static int stage_matvec(dg_mesh* m, Solver* S, const double* U, double t, double c, int jv_mode, int jv_prec,
-                        const double* v, double* out, cudaStream_t s) {
+                        const double* v, double* out, cudaStream_t s, bool value_ready = false) {
   // exact tangent: one fused pass forms M v - c J_r v
-  if (jv_mode == DG_JV_EXACT) return stage_jvp(m, U, v, t, c, out, jv_prec == DG_PREC_F32, s);
+  if (jv_mode == DG_JV_EXACT) return stage_jvp(m, U, v, t, c, out, jv_prec == DG_PREC_F32, s, value_ready);
   double* mv = S->v(VTMP);
   int rc = dg_mass_apply(m, v, mv, s);
   if (rc) return rc;
@@ -1460,6 +1460,14 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
   if (!std::isfinite(bnorm)) return fail(DG_ENAN, "GMRES: non-finite right-hand side");
   if (!x0_given || bnorm == 0.0) DG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   if (bnorm == 0.0) return DG_OK;
+  // every operator application of this solve linearises at the same U: its value plane (Gauss
+  // values, traces, LDG gradient) is formed once; the preconditioners do not touch the workspace
+  bool vr = false;
+  if (o.jv_mode == DG_JV_EXACT && !(o.flags & DG_OPT_RECOMPUTE_VALUE)) {
+    rc = stage_value_plane(m, U, o.jv_prec == DG_PREC_F32, s);
+    if (rc) return rc;
+    vr = true;
+  }
   std::vector<double> H((size_t)(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
   const bool f32gs = o.jv_prec == DG_PREC_F32;
   for (int cycle = 0; cycle < o.max_restarts; ++cycle) {
@@ -1467,7 +1475,7 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
     if (cycle == 0) {
       if (!x0_given) DG_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     } else {
-      rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, x, w, s);
+      rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, x, w, s, vr);
       if (rc) return rc;
       k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0, b, -1.0, w, 0.0, nullptr, r);
       DG_LAUNCH_CHECK("k_lincomb");
@@ -1486,7 +1494,7 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
     for (int k = 0; k < R; ++k) {
       rc = precond_apply(m, S, o.precond, V + (long long)k * n, z, s);
       if (rc) return rc;
-      rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, z, w, s);
+      rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, z, w, s, vr);
       if (rc) return rc;
       // classical Gram-Schmidt twice; h and the norm stay on the device until one read-back. With
       // the FP32 Jv the projections are formed in FP32 arithmetic (orthogonality to ~1e-7, far

@@ -46,7 +46,7 @@ class DgSolverOpts(ctypes.Structure):
         ("max_newton", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_refresh", ctypes.c_int32),
         ("jv_mode", ctypes.c_int32), ("jv_prec", ctypes.c_int32), ("newton_rtol", ctypes.c_double),
         ("gmres_rtol", ctypes.c_double), ("abs_floor", ctypes.c_double), ("rb_size", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
     ]
 
 

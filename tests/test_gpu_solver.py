@@ -154,6 +154,27 @@ def test_solver_variants_reach_the_same_state(torch_cuda):
     assert all(r[0]["status"] == 0 for r in runs.values())
 
 
+@pytest.mark.parametrize("jv_prec", ["f64", "f32"])
+def test_value_plane_once_per_solve_is_bit_identical(torch_cuda, jv_prec):
+    """Forming the state's value plane once per Krylov solve (the default) gives bit for bit the step
+    of recomputing it in every operator application: same states, same iteration counts. The shell
+    has wall and outflow boundaries, where the tangent trace reads the value plane."""
+    torch = torch_cuda
+    from paper_2306_01085_gb300.dg import Mesh
+    d = W.shell_desc(n=2, nr=4, p=2, euv=True)
+    m = Mesh(d)
+    u0 = torch.from_numpy(W.state_for(d, m.nodes().cpu().numpy(), 8)).cuda()
+    dt = 60.0 / W.shell_reference().t0
+    out = {}
+    for flags in (0, 1):
+        u = u0.clone()
+        st = m.implicit_step(u, 0.0, dt, stages=3, precond="bj", jv_prec=jv_prec, flags=flags)
+        out[flags] = (st["gmres"], st["newton"], u.cpu().numpy())
+    m.close()
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2])
+
+
 def test_unpreconditioned_and_block_jacobi_agree(torch_cuda):
     """Unpreconditioned GMRES(30) stalls on this stratified shell once Newton has removed the
     smooth error, so the comparison is one backward-Euler stage of 2.2 s to a Newton tolerance of
