@@ -198,19 +198,42 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
       if (NC == 2) ug[plane_g + e * 5 * NP + rem] = in[(l * C + 5) * NP + rem];
     }
   }
+  // face traces. FP32: one face point per iteration, its N volume points found once (less index
+  // arithmetic); FP64: the flat loop over (face, c, point), which spreads the FP64 work evenly.
   const long long plane_f = E * 6 * 5 * NF;
-  for (int idx = threadIdx.x; idx < EPB * 6 * 5 * NF; idx += blockDim.x) {
-    const int l = idx / (30 * NF), rem = idx % (30 * NF);
-    const int phi = rem / (5 * NF), c = (rem / NF) % 5, f = rem % NF;
-    const long long e = e0 + l;
-    if (e >= E) continue;
-    const R* ev = (phi & 1) ? so.eR : so.eL;
-    for (int pl = 0; pl < NC; ++pl) {
-      const R* src = in + (l * C + 5 * pl + c) * NP;
-      R acc = R(0);
+  if constexpr (sizeof(R) == 4) {
+    for (int idx = threadIdx.x; idx < EPB * 6 * NF; idx += blockDim.x) {
+      const int l = idx / (6 * NF), phi = (idx / NF) % 6, f = idx % NF;
+      const long long e = e0 + l;
+      if (e >= E) continue;
+      const R* ev = (phi & 1) ? so.eR : so.eL;
+      int vp[N];
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
-      uf[pl * plane_f + e * 30 * NF + rem] = acc;
+      for (int k = 0; k < N; ++k) vp[k] = face_vol_point<N>(phi, f, k);
+      for (int pl = 0; pl < NC; ++pl)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const R* src = in + (l * C + 5 * pl + c) * NP;
+          R acc = R(0);
+#pragma unroll
+          for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[vp[k]], acc);
+          uf[pl * plane_f + e * 30 * NF + (phi * 5 + c) * NF + f] = acc;
+        }
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < EPB * 6 * 5 * NF; idx += blockDim.x) {
+      const int l = idx / (30 * NF), rem = idx % (30 * NF);
+      const int phi = rem / (5 * NF), c = (rem / NF) % 5, f = rem % NF;
+      const long long e = e0 + l;
+      if (e >= E) continue;
+      const R* ev = (phi & 1) ? so.eR : so.eL;
+      for (int pl = 0; pl < NC; ++pl) {
+        const R* src = in + (l * C + 5 * pl + c) * NP;
+        R acc = R(0);
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
+        uf[pl * plane_f + e * 30 * NF + rem] = acc;
+      }
     }
   }
 }
@@ -362,28 +385,52 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
     }
     __syncthreads();
   }
-  // write Q (Gauss space) and its face traces
-  for (int idx = threadIdx.x; idx < EPB * 15 * NP; idx += blockDim.x) {
-    const int l = idx / (15 * NP), rem = idx % (15 * NP);
-    const int d = rem / (5 * NP), c = (rem / NP) % 5, gg = rem % NP;
-    const long long e = e0 + l;
-    if (e < E)
-      for (int pl = 0; pl < NC; ++pl)
-        qg[(TO ? E * 15 * NP : 0) + pl * E * 15 * NP + e * 15 * NP + rem] = sQ[((l * 3 + d) * C + 5 * pl + c) * NP + gg];
-  }
-  for (int idx = threadIdx.x; idx < EPB * 6 * 15 * NF; idx += blockDim.x) {
-    const int l = idx / (90 * NF), rem = idx % (90 * NF);
-    const int phi = rem / (15 * NF), dc = (rem / NF) % 15, f = rem % NF;
-    const int d = dc / 5, c = dc % 5;
-    const long long e = e0 + l;
-    if (e >= E) continue;
-    const R* ev = (phi & 1) ? so.eR : so.eL;
-    for (int pl = 0; pl < NC; ++pl) {
-      const R* src = sQ + ((l * 3 + d) * C + 5 * pl + c) * NP;
-      R acc = R(0);
+  // write Q (Gauss space): each thread its own point, the 15 (d, c) entries unrolled. For FP32 the
+  // face traces go one face point per iteration with its N volume points found once (the kernel is
+  // bound by instruction issue, much of it index arithmetic); the FP64 kernel is bound by the FP64
+  // pipe, and there the flat loop over (face, d, c, point) keeps every thread equally busy.
+  if (active) {
+    const long long e = e0 + el;
+    for (int pl = 0; pl < NC; ++pl)
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
-      qf[(TO ? E * 90 * NF : 0) + pl * E * 90 * NF + e * 90 * NF + rem] = acc;
+      for (int dc = 0; dc < 15; ++dc)
+        qg[(TO ? E * 15 * NP : 0) + pl * E * 15 * NP + e * 15 * NP + dc * NP + g] =
+            sQ[((el * 3 + dc / 5) * C + 5 * pl + dc % 5) * NP + g];
+  }
+  if constexpr (sizeof(R) == 4) {
+    for (int idx = threadIdx.x; idx < EPB * 6 * NF; idx += blockDim.x) {
+      const int l = idx / (6 * NF), phi = (idx / NF) % 6, f = idx % NF;
+      const long long e = e0 + l;
+      if (e >= E) continue;
+      const R* ev = (phi & 1) ? so.eR : so.eL;
+      int vp[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) vp[k] = face_vol_point<N>(phi, f, k);
+      for (int pl = 0; pl < NC; ++pl)
+#pragma unroll
+        for (int dc = 0; dc < 15; ++dc) {
+          const R* src = sQ + ((l * 3 + dc / 5) * C + 5 * pl + dc % 5) * NP;
+          R acc = R(0);
+#pragma unroll
+          for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[vp[k]], acc);
+          qf[(TO ? E * 90 * NF : 0) + pl * E * 90 * NF + e * 90 * NF + (phi * 15 + dc) * NF + f] = acc;
+        }
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < EPB * 6 * 15 * NF; idx += blockDim.x) {
+      const int l = idx / (90 * NF), rem = idx % (90 * NF);
+      const int phi = rem / (15 * NF), dc = (rem / NF) % 15, f = rem % NF;
+      const int d = dc / 5, c = dc % 5;
+      const long long e = e0 + l;
+      if (e >= E) continue;
+      const R* ev = (phi & 1) ? so.eR : so.eL;
+      for (int pl = 0; pl < NC; ++pl) {
+        const R* src = sQ + ((l * 3 + d) * C + 5 * pl + c) * NP;
+        R acc = R(0);
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc = cm_fma<CM>(ev[k], src[face_vol_point<N>(phi, f, k)], acc);
+        qf[(TO ? E * 90 * NF : 0) + pl * E * 90 * NF + e * 90 * NF + rem] = acc;
+      }
     }
   }
 }

@@ -227,6 +227,8 @@ CONFIGS = {
                            "transport and four-absorber EUVAC heating, June solstice"),
     "shell48x16_p3_euv": (lambda: shell_desc(n=48, nr=16, p=3, euv=True),
                           "cubed-sphere shell 6x48x48x16, p=3, EUV"),
+    "shell24x8_p3_euv": (lambda: shell_desc(n=24, nr=8, p=3, euv=True),
+                         "cubed-sphere shell 6x24x24x8, p=3, EUV (small profiling case, 8.8M DOF)"),
 }
 
 
