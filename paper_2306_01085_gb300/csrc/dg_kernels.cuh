@@ -664,10 +664,11 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
 
 // stage_c != 0 (NC = 2): the tangent output is the DIRK stage operator J_G v = M v - stage_c J_r v,
 // M v = B^T (W B v) being formed from the tangent's own Gauss values
-// FP32: two CTAs per SM, since the value + tangent physics would otherwise take enough registers to
-// halve the resident warps of this latency-bound kernel (FP64 is bound by its pipe instead)
+// FP32: at least two CTAs per SM (four at p = 3, where 128 registers suffice without spills), since
+// the value + tangent physics would otherwise take enough registers to halve the resident warps of
+// this latency-bound kernel (FP64 is bound by its pipe instead)
 template <int N, int NC, typename R, int CM = CM_NATIVE>
-__global__ void __launch_bounds__(Epb<N, NC>::value * Shape<N>::NP, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(Epb<N, NC>::value * Shape<N>::NP, sizeof(R) == 4 ? (N == 4 ? 4 : 2) : 1)
 k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
                          const R* __restrict__ geo, const R* __restrict__ accg,
                          const R* __restrict__ xg, const R* __restrict__ ug,
