@@ -662,19 +662,28 @@ __device__ __forceinline__ void volume_point(const PhysT<R>& P, const S u[5], co
   for (int c = 0; c < 5; ++c) src[c] = src[c] * Wd;
 }
 
+// L2 prefetch hint for n consecutive elements from p, one 128-byte line per thread and iteration
+template <typename R>
+__device__ __forceinline__ void prefetch_l2(const R* p, long long n) {
+  const char* c = reinterpret_cast<const char*>(p);
+  const long long bytes = n * (long long)sizeof(R);
+  for (long long off = threadIdx.x * 128LL; off < bytes; off += blockDim.x * 128LL)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
+}
+
 // stage_c != 0 (NC = 2): the tangent output is the DIRK stage operator J_G v = M v - stage_c J_r v,
 // M v = B^T (W B v) being formed from the tangent's own Gauss values
-// FP32: at least two CTAs per SM (four at p = 3, where 128 registers suffice without spills), since
+// FP32: at least two CTAs per SM (four for the p = 3 Jv, where 128 registers suffice without spills), since
 // the value + tangent physics would otherwise take enough registers to halve the resident warps of
 // this latency-bound kernel (FP64 is bound by its pipe instead)
 template <int N, int NC, typename R, int CM = CM_NATIVE>
-__global__ void __launch_bounds__(Epb<N, NC>::value * Shape<N>::NP, sizeof(R) == 4 ? (N == 4 ? 4 : 2) : 1)
+__global__ void __launch_bounds__(Epb<N, NC>::value * Shape<N>::NP, sizeof(R) == 4 ? (N == 4 && NC == 2 ? 4 : 2) : 1)
 k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
                          const R* __restrict__ geo, const R* __restrict__ accg,
                          const R* __restrict__ xg, const R* __restrict__ ug,
                          const R* __restrict__ qg, const R* __restrict__ fh,
                          double* __restrict__ r, double* __restrict__ jv, R stage_c,
-                         const R* __restrict__ mixg) {
+                         const R* __restrict__ mixg, long long ahead) {
   using S = typename std::conditional<NC == 2, DualT<R>, R>::type;
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
   __shared__ SmemOpsT<R> so;
@@ -686,6 +695,23 @@ k_volume(long long E, const Ops* __restrict__ ops, PhysT<R> P, R t,
   R* sT = sR + EPB * C * NP;                // [EPB][C][NP]
   load_ops<N, R>(ops, so);
   const long long e0 = (long long)blockIdx.x * EPB;
+  if constexpr (sizeof(R) == 4) {
+    // FP32 is latency-bound on these loads: pull into L2 the records of the CTA `ahead` launches
+    // later (one residency wave, so it starts about when this one ends)
+    const long long eb = e0 + ahead * EPB;
+    if (ahead > 0 && eb < E) {
+      const long long ne = (E - eb < EPB) ? E - eb : EPB;
+      for (int pl = 0; pl < NC; ++pl) {
+        prefetch_l2(ug + pl * E * 5 * NP + eb * 5 * NP, ne * 5 * NP);
+        prefetch_l2(qg + pl * E * 15 * NP + eb * 15 * NP, ne * 15 * NP);
+        prefetch_l2(fh + pl * E * 30 * NF + eb * 30 * NF, ne * 30 * NF);
+      }
+      prefetch_l2(geo + eb * 10 * NP, ne * 10 * NP);
+      prefetch_l2(accg + eb * 3 * NP, ne * 3 * NP);
+      if (P.euv) prefetch_l2(xg + eb * 3 * NP, ne * 3 * NP);
+      if (P.comp) prefetch_l2(mixg + eb * 8 * NP, ne * 8 * NP);
+    }
+  }
   const long long plane_f = E * 30 * NF;
   for (int idx = threadIdx.x; idx < EPB * 30 * NF; idx += blockDim.x) {
     const int l = idx / (30 * NF), rem = idx % (30 * NF);
@@ -1171,9 +1197,20 @@ static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t 
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
   const WorkT<R> w = work_of<R>(m);
+  // CTAs resident at once (the prefetch distance of the FP32 kernel)
+  static long long resident = -1;
+  if (resident < 0) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_volume<N, NC, R, CM>, EPB * NP, sm) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = sms = 0;
+    }
+    resident = (long long)per_sm * sms;
+  }
   prof_begin(m, s, KK_VOLUME);
   k_volume<N, NC, R, CM><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), (R)t, w.geo, w.acc, w.xg,
-                                                   w.ug, w.qg, w.fh, r, jv, (R)stage_c, w.mixg);
+                                                   w.ug, w.qg, w.fh, r, jv, (R)stage_c, w.mixg, resident);
   prof_end(m, s);
   DG_LAUNCH_CHECK("k_volume");
   return DG_OK;
