@@ -190,7 +190,7 @@ FP64_FLOPS_PER_ELEMENT = {("k_grad", 5): float(grad_flops_per_element(5)), ("k_v
 FLOPS_KIND = {"k_grad": "algorithmic (sum-factorisation count)", "k_volume": "executed (ncu instruction counts)",
               "k_faces": "executed (ncu instruction counts)"}
 DRAM_BYTES_PER_LAUNCH = {("k_grad", 5): 1206108672.0, ("k_volume", 5): 912022272.0, ("k_faces", 5): 755261952.0}
-CAPTURE_DIGEST = "5c73cd67134907dc02bc41287fadc2956d8859c6b72a368848edd7183f61e2f9"
+CAPTURE_DIGEST = "a3a5ace70bb03005accaf9eafe37c37425512c87388f0f7d4384474e5ccbcaba"
 RESIDUAL_SOURCES = ("dg_kernels.cuh", "dg_internal.cuh", "dg_map.cuh", "dg_kernels_n5.cu")
 
 

@@ -263,7 +263,8 @@ typedef struct dg_solver_opts {
 } dg_solver_opts;
 
 /* dg_solver_opts.flags: recompute the state's Gauss values, traces and LDG gradient in every
- * operator application instead of once per Krylov solve (same results; for checking). */
+ * operator application and every block-assembly sweep, instead of once per Krylov solve and once
+ * per assembly (same results; for checking). */
 #define DG_OPT_RECOMPUTE_VALUE 1
 
 typedef struct dg_step_stats {

@@ -189,7 +189,7 @@ struct Driver {
   static int mixture(dg_mesh* m);
   // J_r probe restricted to each element's own diagonal block (exact, one column per element)
   static int jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s,
-                          bool f32 = false);
+                          bool f32 = false, bool tangent_only = false);
   // FP32 residual (v == NULL) or fused residual + exact Jv with a contraction mode (CM_*)
   static int eval_cm(dg_mesh* m, const double* u, const double* v, double t, double* r, double* jv, int cm,
                      cudaStream_t s);
@@ -200,7 +200,8 @@ struct Driver {
   template <typename R>
   static int residual_p(dg_mesh* m, double t, double* r, double* jv, bool tangent, cudaStream_t s, double stage_c);
   template <typename R>
-  static int jv_blockdiag_p(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s);
+  static int jv_blockdiag_p(dg_mesh* m, const double* u, const double* probe, double t, double* jv, cudaStream_t s,
+                            bool tangent_only);
 };
 
 // orientation map of face point (is, it) to the neighbour's face point index

@@ -246,16 +246,16 @@ __global__ void k_interp(const double* __restrict__ u, const double* __restrict_
 // the gradient tangent this element would get from its neighbour's perturbation across that face:
 // kappa(f) (w n dS)(f) u_dot_nb(f) / 2 with kappa(f) = sum_k e_face[k]^2 / (w |J|)(g(f, k)).
 // TO (tangent only, NC = 1): the value plane of ug, uf, qg, qf already holds the state's values
-// (computed once for all the Jv of one Krylov solve); only the tangent plane is formed, with the
-// same arithmetic as the tangent of NC = 2, so the result is identical. The wall trace of the
-// tangent reads the value plane's varrho trace.
+// (computed once for all the Jv of one Krylov solve, or for all the probes of one block assembly);
+// only the tangent plane is formed, with the same arithmetic as the tangent of NC = 2, so the
+// result is identical. The wall trace of the tangent reads the value plane's varrho trace.
 template <int N, int NC, bool BLK, typename R, int CM = CM_NATIVE, bool TO = false>
 __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, const R* __restrict__ geo,
                        const R* __restrict__ fgeo, const int* __restrict__ nbr,
                        const int* __restrict__ nbr_fo, const R* __restrict__ ug,
                        const R* __restrict__ uf, R* __restrict__ qg, R* __restrict__ qf,
                        R* __restrict__ qx) {
-  static_assert(!TO || (NC == 1 && !BLK), "tangent-only gradient works on one plane");
+  static_assert(!TO || NC == 1, "tangent-only gradient works on one plane");
   constexpr int NP = Shape<N>::NP, NF = Shape<N>::NF, C = 5 * NC, EPB = Epb<N, NC>::value;
   __shared__ SmemOpsT<R> so;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -295,9 +295,10 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
       for (int pl = 0; pl < NC; ++pl)
         for (int c = 0; c < 5; ++c) oth[5 * pl + c] = uf[of + pl * plane_f + nbase + c * NF];
       if constexpr (BLK) {
+        constexpr int T0 = TO ? 0 : 5;   // where the tangent sits in own / oth / dst
         for (int c = 0; c < 5; ++c) {
-          dst[c * NF] = R(0.5) * (own[c] + oth[c]);
-          dst[(5 + c) * NF] = R(0.5) * own[5 + c];
+          if constexpr (!TO) dst[c * NF] = R(0.5) * (own[c] + oth[c]);
+          dst[(T0 + c) * NF] = R(0.5) * own[T0 + c];
         }
         const R* ev = (phi & 1) ? so.eR : so.eL;
         R kappa = R(0);
@@ -305,7 +306,7 @@ __global__ void k_grad(long long E, const Ops* __restrict__ ops, PhysT<R> P, con
         R* xo = qx + (e * 6 + phi) * 15 * NF + f;
         for (int d = 0; d < 3; ++d) {
           const R kn = R(0.5) * kappa * fgeo[((e * 6 + phi) * 4 + d) * NF + f];
-          for (int c = 0; c < 5; ++c) xo[(d * 5 + c) * NF] = kn * oth[5 + c];
+          for (int c = 0; c < 5; ++c) xo[(d * 5 + c) * NF] = kn * oth[T0 + c];
         }
       } else {
         for (int c = 0; c < C; ++c) dst[c * NF] = R(0.5) * (own[c] + oth[c]);
@@ -1271,10 +1272,17 @@ int Driver<N>::residual(dg_mesh* m, const double* u, const double* v, double t, 
 template <int N>
 template <typename R>
 int Driver<N>::jv_blockdiag_p(dg_mesh* m, const double* u, const double* probe, double t, double* jv,
-                              cudaStream_t s) {
-  int rc = run_interp<N, 2, R>(m, u, probe, s);
-  if (rc) return rc;
-  rc = run_grad<N, 2, true, R>(m, s);
+                              cudaStream_t s, bool tangent_only) {
+  int rc;
+  if (tangent_only) {   // u's value plane is in place
+    rc = run_interp_tangent<N, R>(m, probe, s);
+    if (rc) return rc;
+    rc = run_grad<N, 1, true, R, CM_NATIVE, true>(m, s);
+  } else {
+    rc = run_interp<N, 2, R>(m, u, probe, s);
+    if (rc) return rc;
+    rc = run_grad<N, 2, true, R>(m, s);
+  }
   if (rc) return rc;
   rc = run_faces<N, 2, true, R>(m, s);
   if (rc) return rc;
@@ -1283,8 +1291,9 @@ int Driver<N>::jv_blockdiag_p(dg_mesh* m, const double* u, const double* probe, 
 
 template <int N>
 int Driver<N>::jv_blockdiag(dg_mesh* m, const double* u, const double* probe, double t, double* jv,
-                            cudaStream_t s, bool f32) {
-  return f32 ? jv_blockdiag_p<float>(m, u, probe, t, jv, s) : jv_blockdiag_p<double>(m, u, probe, t, jv, s);
+                            cudaStream_t s, bool f32, bool tangent_only) {
+  return f32 ? jv_blockdiag_p<float>(m, u, probe, t, jv, s, tangent_only)
+             : jv_blockdiag_p<double>(m, u, probe, t, jv, s, tangent_only);
 }
 
 template <int N>

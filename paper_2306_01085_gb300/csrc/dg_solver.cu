@@ -853,6 +853,7 @@ struct Solver {
   int* piv = nullptr;
   int* info = nullptr;
   bool bj_ready = false;
+  bool recompute_value = false;  // DG_OPT_RECOMPUTE_VALUE of the running implicit step
   __half* blocks_h = nullptr;  // [E][5Np][ld]: FP16 columns of the inverses (DG_PC_BJ16)
   float* hscale = nullptr;     // [E][5Np]: their power-of-two column scales
   int hld = 0;
@@ -1076,11 +1077,18 @@ static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double 
   const int nb = 5 * m->np;
   double* jv = S->v(VW);
   double* mv = S->v(VTMP);
+  // every probe linearises at the same U: its value plane is formed once and each sweep
+  // differentiates the probe's tangent alone
+  const bool once = !S->recompute_value;
+  if (once) {
+    rc = stage_value_plane(m, U, f32, s);
+    if (rc) return rc;
+  }
   for (int j = 0; j < nb; ++j) {
     prof_begin(m, s, KK_BLAS);
     k_probe<<<grid_for(S->n), 256, 0, s>>>(m->E, nb, j, S->probe);
     prof_end(m, s);
-    DG_DISPATCH_S(m, jv_blockdiag(m, U, S->probe, t, jv, s, f32));
+    DG_DISPATCH_S(m, jv_blockdiag(m, U, S->probe, t, jv, s, f32, once));
     if (rc) return rc;
     DG_DISPATCH_S(m, mass(m, S->probe, mv, s, f32));   // FP32 arithmetic for FP32 blocks
     if (rc) return rc;
@@ -1653,6 +1661,11 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
     rc = ensure_rb(S, o.rb_size);
     if (rc) return rc;
   }
+  struct FlagScope {   // the flag holds for this step's block assemblies only
+    Solver* S;
+    ~FlagScope() { S->recompute_value = false; }
+  } flag_scope{S};
+  S->recompute_value = (o.flags & DG_OPT_RECOMPUTE_VALUE) != 0;
   dg_step_stats st;
   std::memset(&st, 0, sizeof(st));
   const long long n = S->n;

@@ -157,9 +157,10 @@ def test_solver_variants_reach_the_same_state(torch_cuda):
 @pytest.mark.parametrize("p", [2, 3])
 @pytest.mark.parametrize("jv_prec", ["f64", "f32"])
 def test_value_plane_once_per_solve_is_bit_identical(torch_cuda, jv_prec, p):
-    """Forming the state's value plane once per Krylov solve (the default) gives bit for bit the step
-    of recomputing it in every operator application: same states, same iteration counts. The shell
-    has wall and outflow boundaries, where the tangent trace reads the value plane."""
+    """Forming the state's value plane once per Krylov solve and once per block assembly (the
+    default) gives bit for bit the step of recomputing it in every operator application and every
+    assembly sweep: same states, same iteration counts. The shell has wall and outflow boundaries,
+    where the tangent trace reads the value plane."""
     torch = torch_cuda
     from paper_2306_01085_gb300.dg import Mesh
     d = W.shell_desc(n=2, nr=4, p=p, euv=True)
