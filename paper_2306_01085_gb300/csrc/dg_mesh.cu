@@ -584,8 +584,8 @@ extern "C" int dg_residual(dg_mesh* mesh, const double* u, const double* q, doub
 
 namespace dg {
 
-__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b,
-                        const double* __restrict__ y, double* __restrict__ out) {
+// out may alias x or y (each entry is read before it is written, by the same thread)
+__global__ void k_axpby(long long n, double a, const double* x, double b, const double* y, double* out) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = a * x[i] + b * (y ? y[i] : 0.0);
 }

@@ -111,9 +111,10 @@ constexpr int RED_THREADS = 256;
 constexpr int MAXK = 64;          // largest restart + 1
 constexpr int RB_MAX = 16;        // largest reduced basis
 
-__global__ void k_lincomb(long long n, double a, const double* __restrict__ x, double b,
-                          const double* __restrict__ y, double c, const double* __restrict__ z,
-                          double* __restrict__ out) {
+// out = a x + b y + c z; out may alias any input (each entry is read before it is written, by the
+// same thread)
+__global__ void k_lincomb(long long n, double a, const double* x, double b, const double* y, double c,
+                          const double* z, double* out) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double v = a * x[i];
     if (y) v = fma(b, y[i], v);
@@ -123,8 +124,7 @@ __global__ void k_lincomb(long long n, double a, const double* __restrict__ x, d
 }
 
 // out = x * (*scale_num) / sqrt(*scale_den)  (device-resident scalars)
-__global__ void k_scale_dev(long long n, const double* __restrict__ x, const double* __restrict__ den,
-                            double* __restrict__ out) {
+__global__ void k_scale_dev(long long n, const double* x, const double* __restrict__ den, double* out) {
   const double s = 1.0 / sqrt(*den);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = x[i] * s;
@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot_k(long long n2, c
   constexpr int NR = (DOTS && SMALL) ? K + 1 : 1;   // register accumulators (last: |w|^2)
   extern __shared__ double sacc[];                  // SACC: [K][RED_THREADS]
   __shared__ double hs[K > 0 ? K : 1];
-  if (threadIdx.x < K) hs[threadIdx.x] = h[threadIdx.x];
+  if constexpr (K > 0)
+    if (threadIdx.x < K) hs[threadIdx.x] = h[threadIdx.x];
   if constexpr (SACC)
     for (int j = 0; j < K; ++j) sacc[j * RED_THREADS + threadIdx.x] = 0.0;
   __syncthreads();
