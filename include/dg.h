@@ -254,7 +254,8 @@ typedef struct dg_solver_opts {
     int32_t precond;         /* DG_PC_* */
     int32_t precond_refresh; /* DG_REFRESH_* */
     int32_t jv_mode;         /* DG_JV_EXACT or DG_JV_FD for the GMRES operator */
-    int32_t jv_prec;         /* DG_PREC_F64, or DG_PREC_F32: FP32 inner Jv and block assembly (mixed) */
+    int32_t jv_prec;         /* DG_PREC_F64, or DG_PREC_F32 (mixed): FP32 inner Jv, block assembly and
+                                Gram-Schmidt arithmetic on the FP64 Krylov basis */
     double newton_rtol;      /* stop when ||G||_2 <= newton_rtol ||G(U^0)||_2 (1e-8) */
     double gmres_rtol;       /* each Newton system to ||b - J x|| <= gmres_rtol ||b|| (1e-3) */
     double abs_floor;        /* or when ||G||_2 <= abs_floor ||M U||_2 (1e-14) */
@@ -303,8 +304,10 @@ int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, const dg_sol
  * inference for every element; see dg_mlp_init).
  * DG_PC_BJ: the exact diagonal block of every element (including the path through the
  * neighbours' LDG gradients) is computed column by column by block-diagonal tangent sweeps and
- * inverted in place in FP32 by Gauss-Jordan elimination with partial pivoting, so that applying
- * the preconditioner is one coalesced dense product per element. Synchronises the stream.
+ * inverted in place in FP32 by Gauss-Jordan elimination with partial pivoting (one CTA per block in
+ * shared memory, or a thread-block cluster sharing the block's columns when it does not fit), so
+ * that applying the preconditioner is one coalesced dense product per element. Synchronises the
+ * stream.
  * DG_ENAN on a zero pivot.
  * DG_PC_BJ16: as DG_PC_BJ, then every column j of an inverse is divided by the power of two c_j
  * just above its largest magnitude and rounded to FP16 (relative error 2^-11 per entry down to
