@@ -218,9 +218,10 @@ int dg_mass_inverse_apply(dg_mesh* mesh, const double* v, double* mv, void* stre
  * (a file-scope __device__ array that every GPU loading the library holds until process exit).
  * A mesh needs n_elem (20 n_p + 150 (p+1)^2) doubles of it, so at most 1,109 elements at p = 2,
  * 569 at p = 3 and 335 at p = 4; larger meshes are rejected with DG_EINVAL and a message giving
- * both sizes. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture. All calls share the one array and every call
+ * both sizes. The array becomes resident on a device when the first mesh is created there:
+ * dg_mesh_create looks up its device address (cudaGetSymbolAddress, with that device current,
+ * which also loads the module holding it) and keeps it in the mesh, so this call does no set-up of
+ * its own. All calls share the one array and every call
  * overwrites what it reads before reading it, so nothing needs clearing between calls; calls that
  * overlap on the GPU (other streams, other threads) race on the array and must be serialised by
  * the caller. The mesh itself (geometry, connectivity) is allocated by dg_mesh_create as usual.

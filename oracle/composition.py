@@ -18,7 +18,7 @@ alpha_O = alpha_He = 5.6e-4, nu_e = nu_eddy/nu_0 = 200 and alpha_e = alpha_eddy/
 -(1/c_v)(sqrt(rho) T v - c_kappa kappa/(sqrt(rho) c_v) grad T) . grad c_v, with grad c_v from the
 fits' radial derivative.
 
-Readings (listed in the design doc): the fit coefficients are inputs (the paper fits them to MSIS, which
+Readings of the paper taken here: the fit coefficients are inputs (the paper fits them to MSIS, which
 is not available; the workloads carry synthetic ones); gamma stays 5/3; in this mode the paper's
 transport laws replace the T^visc_exp law; the EUVAC optical depth of a band sums over the species
 (photons are absorbed by every constituent).

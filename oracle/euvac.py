@@ -19,7 +19,7 @@ phi~ = mod_2pi(phi_0 + omega t): cos chi = sin(delta) sin(theta) + cos(delta) co
 delta = arcsin(sin(-delta_0) cos(2 pi/365.24 (N_d + 9) + 2 e sin(2 pi/365.24 (N_d - 3)))),
 delta_0 = 23.44 deg, e = 0.0167.
 
-Readings (listed in DESIGN.md): the flux column of the appendix table is printed as "x 10^-13
+Readings of the paper taken here: the flux column of the appendix table is printed as "x 10^-13
 (m^-2 s^-1)"; photon fluxes of 10^13 m^-2 s^-1 are meant (EUVAC fluxes are 10^9 cm^-2 s^-1). The
 photon energy of a wavelength band is taken at its centre, of a line at the line. Only the oxygen
 cross sections enter (the model's single constituent); the exp(y^2) erfc(y) products are evaluated

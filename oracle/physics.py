@@ -5,7 +5,7 @@ LDG gradient, q[d, c] ~ d u_c / d x_d. All functions take arrays with trailing p
 u (5, ...), q (3, 5, ...), x (3, ...), and work for any numpy dtype (float64, complex128), so the
 complex-step derivative of everything built on them is exact to rounding.
 
-Reading of the paper (every point is also listed in the design doc):
+Reading of the paper taken here:
   * sqrt(rho) = exp(varrho / 2); v = u_{2:4} exp(-varrho/2); T = u_5 exp(-varrho/2).
   * grad v = exp(-varrho/2) (grad u_m - u_m grad(varrho) / 2), grad T likewise (chain rule on q).
   * Coefficients of Eq. fluxSWNondimensional: c_mu = 1/sqrt(gamma Gr), c_kappa = sqrt(gamma/Gr)/Pr,

@@ -3,7 +3,7 @@
 Sec. 3.2 preconditions each Newton system J dU = -G (Eq. NewtonSolve) with a low-rank
 approximation of the Jacobian built on the reduced-basis space W_n spanned by the last n_rb Newton
 updates, and uses the same space for the initial guess of GMRES. The construction itself is left to
-the paper's references; the reading taken here (listed in the design doc):
+the paper's references; the reading taken here:
 
   * W is any basis of the RB space (its span is all that matters), Z = J W its image under the
     stage Jacobian J = J_G (n_rb Jacobian-vector products, matrix-free);

@@ -9,7 +9,7 @@ needs only Jacobian-vector products. Stage i of an s-stage DIRK:
 so the Newton residual is G(U) = M (U - u_n) - dt sum_{j<i} a_ij r(U_j) - dt a_ii r(U) and its
 Jacobian J_G v = M v - dt a_ii J_r v.
 
-Readings (listed in the design doc): Newton stops when ||G||_2 <= tol ||G(U^0)||_2 with U^0 the previous
+Readings of the paper taken here: Newton stops when ||G||_2 <= tol ||G(U^0)||_2 with U^0 the previous
 stage value (absolute floor 1e-14 ||M U||_2); GMRES(restart) solves each Newton system to a
 fixed relative tolerance eta; the block-Jacobi blocks are the exact diagonal blocks of J_G.
 

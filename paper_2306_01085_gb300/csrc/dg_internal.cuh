@@ -99,6 +99,15 @@ struct WorkT {
   const R *geo, *fgeo, *acc, *xg;
   const R *mixg, *mixf;   // variable composition at Gauss / face points (NULL without it)
 };
+// resident CTAs per device of a kernel at a launch shape, looked up once per mesh (the mesh fixes
+// the device) and kernel instance
+struct OccCache {
+  static constexpr int CAP = 32;
+  const void* fn[CAP] = {};
+  size_t smem[CAP] = {};
+  long long val[CAP] = {};
+  int n = 0;
+};
 struct Prof {
   bool on = false;
   int cap = 0, used = 0;
@@ -111,6 +120,7 @@ struct Prof {
 struct dg_mesh {
   dg_mesh_desc desc;
   dg::Prof prof;
+  dg::OccCache occ;
   int n, np, nf;           // points per direction, per element, per face
   int64_t E, ndof, nfaces;
   int device;
@@ -133,12 +143,16 @@ struct dg_mesh {
   dg::WorkT<float> w32 = {};        // FP32 workspace and geometry, created on first FP32 call
   float* w32_base = nullptr;
   dg::Mlp* mlp = nullptr;           // learned preconditioner, created by dg_mlp_init
+  double* static_scratch = nullptr; // device address of dg_residual_static's array on this device
 };
 
 void dg_mlp_release(dg_mesh* m);
 
 namespace dg {
 int ensure_f32(dg_mesh* m);       // allocate and fill the FP32 workspace and geometry
+// device address of dg_residual_static's scratch array on the current device dev (looked up once
+// per device; the lookup loads the module that holds the array)
+int static_scratch_address(int dev, double** out);
 }
 int mlp_setup(dg_mesh* mesh, const double* u, double dt_aii, cudaStream_t s);
 // J_G v = M v - c J_r(u) v in one tangent pass (exact tangent; FP32 arithmetic when f32). With

@@ -1190,6 +1190,28 @@ static int run_faces(dg_mesh* m, cudaStream_t s) {
   return DG_OK;
 }
 
+// resident CTAs of kernel fn on the mesh's device at this launch shape (0 if the query fails),
+// cached in the mesh
+inline long long resident_ctas(dg_mesh* m, const void* fn, int threads, size_t smem) {
+  OccCache& c = m->occ;
+  for (int i = 0; i < c.n; ++i)
+    if (c.fn[i] == fn && c.smem[i] == smem) return c.val[i];
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = sms = 0;
+  }
+  const long long v = (long long)per_sm * sms;
+  if (c.n < OccCache::CAP) {
+    c.fn[c.n] = fn;
+    c.smem[c.n] = smem;
+    c.val[c.n] = v;
+    c.n++;
+  }
+  return v;
+}
+
 template <int N, int NC, typename R = double, int CM = CM_NATIVE>
 static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t s, double stage_c = 0.0) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
@@ -1198,17 +1220,8 @@ static int run_volume(dg_mesh* m, double t, double* r, double* jv, cudaStream_t 
   if (rc) return rc;
   const unsigned blocks = (unsigned)((m->E + EPB - 1) / EPB);
   const WorkT<R> w = work_of<R>(m);
-  // CTAs resident at once (the prefetch distance of the FP32 kernel)
-  static long long resident = -1;
-  if (resident < 0) {
-    int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_volume<N, NC, R, CM>, EPB * NP, sm) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess) {
-      cudaGetLastError();
-      per_sm = sms = 0;
-    }
-    resident = (long long)per_sm * sms;
-  }
+  // CTAs resident at once (the prefetch distance of the FP32 kernel), per mesh and kernel instance
+  const long long resident = resident_ctas(m, (const void*)k_volume<N, NC, R, CM>, EPB * NP, sm);
   prof_begin(m, s, KK_VOLUME);
   k_volume<N, NC, R, CM><<<blocks, EPB * NP, sm, s>>>(m->E, m->d_ops, phys_as<R>(m->phys), (R)t, w.geo, w.acc, w.xg,
                                                    w.ug, w.qg, w.fh, r, jv, (R)stage_c, w.mixg, resident);

@@ -528,6 +528,8 @@ extern "C" int dg_mesh_create(const dg_mesh_desc* desc, const double* nodes, dg_
     rc = dalloc(&m->mixg, E * 8 * NP) | dalloc(&m->mixf, E * 12 * NF);
     if (rc == DG_OK) rc = drv_mixture(m);
   }
+  // the allocation-free residual's scratch array becomes resident here, where allocating is allowed
+  if (rc == DG_OK) rc = static_scratch_address(m->device, &m->static_scratch);
   if (rc == DG_OK) err = cudaDeviceSynchronize();
   if (rc != DG_OK || err != cudaSuccess) {
     free_mesh(m);

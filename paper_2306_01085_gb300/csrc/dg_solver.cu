@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
+#include "dg_bits.cuh"
 #include "dg_internal.cuh"
 
 namespace dg {
@@ -330,24 +331,7 @@ __global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot_k(long long n2, c
 }
 
 // FP32 Gram-Schmidt arithmetic on the FP64 basis (the mixed-precision solve, whose Jv is itself
-// FP32). On this GPU a cvt between FP64 and FP32 issues on the FP64 pipe, as slowly as a DFMA, so
-// the conversions are done on the integer pipe from the IEEE-754 bit layouts: to_f32 truncates the
-// significand to 24 bits (relative error below 2^-23) and flushes magnitudes under 2^-126 to zero;
-// to_f64 is exact for normal floats and flushes subnormal ones.
-__device__ __forceinline__ float to_f32(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const unsigned e = (hi >> 20) & 0x7ffu;
-  const unsigned ef = e < 897u ? 0u : (e > 1150u ? 254u : e - 896u);
-  const unsigned m = ef ? (((hi & 0xfffffu) << 3) | (lo >> 29)) : 0u;
-  return __uint_as_float((hi & 0x80000000u) | (ef << 23) | m);
-}
-
-__device__ __forceinline__ double to_f64(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned e = (b >> 23) & 0xffu;
-  const unsigned hi = (b & 0x80000000u) | (e ? ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3) : 0u);
-  return __hiloint2double((int)hi, (int)(e ? b << 29 : 0u));
-}
+// FP32), with the integer-pipe conversions to_f32 / to_f64 of dg_bits.cuh.
 
 // k_mdot_k with FP32 products and per-thread FP32 sums (cross-thread sums in FP64); the |w|^2 row
 // stays FP64.

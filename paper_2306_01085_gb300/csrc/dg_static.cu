@@ -20,10 +20,14 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 double* g_static_ptr[kMaxDevices] = {nullptr};
+}  // namespace
 
-// device address of the scratch array on the current device (looked up once per device; the
-// array's name in host code is only a host-side stand-in, never a device address)
+// Device address of the scratch array on the current device dev, looked up once per device (the
+// array's name in host code is only a host-side stand-in, never a device address). With lazy
+// module loading the lookup is what loads the module holding the array and reserves its 16 MiB,
+// so dg_mesh_create calls it, and dg_residual_static only reads the address the mesh keeps.
 int static_scratch_address(int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(DG_EINVAL, "static scratch: device index out of range");
   std::lock_guard<std::mutex> lock(g_static_mu);
   if (!g_static_ptr[dev]) {
     void* p = nullptr;
@@ -36,6 +40,7 @@ int static_scratch_address(int dev, double** out) {
   return DG_OK;
 }
 
+namespace {
 template <int N>
 int static_residual(dg_mesh* view, const double* u, double t, double* r, cudaStream_t s) {
   int rc = Driver<N>::gradient(view, u, nullptr, s);
@@ -60,10 +65,8 @@ extern "C" int dg_residual_static(dg_mesh* mesh, const double* u, double t, doub
   int dev = 0;
   DG_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != mesh->device) return fail(DG_EINVAL, "dg_residual_static: current device is not the mesh's device");
-  if (dev < 0 || dev >= kMaxDevices) return fail(DG_EINVAL, "dg_residual_static: device index out of range");
-  double* base = nullptr;
-  int rc = static_scratch_address(dev, &base);
-  if (rc) return rc;
+  double* base = mesh->static_scratch;   // looked up by dg_mesh_create on this device
+  if (!base) return fail(DG_ECUDA, "dg_residual_static: the mesh holds no scratch address");
   // a view of the mesh that shares its geometry and points its workspace into the static array
   dg_mesh view = *mesh;
   view.prof = Prof();

@@ -3,7 +3,12 @@
 This module is the one place both the CUDA path and the CPU oracle take their inputs from. It holds
 no arithmetic of the discretisation: no basis, quadrature, geometry, flux or residual. It only
 states *which problem* is solved (the domain description, the nondimensional numbers of the model in
-Sec. 2.4, the base atmosphere and the seeded perturbations) and draws random numbers.
+Sec. 2.4, the base atmosphere and the seeded perturbations) and draws random numbers. Since both
+sides read what it computes, each of its computations is pinned on its own by
+tests/test_workload_pins.py: the reference scales (hand values and algebraic identities of the
+definitions), the hydrostatic state (a closed form and an independent ODE integration), the
+cubed-sphere node map (layer radii, equal angles, cube-diagonal corners) and SplitMix64 (the
+reference generator's published outputs).
 
 State functions take node coordinates as an argument, so each side evaluates them on its own mesh
 (the oracle on its nodes for parity tests; the benchmark on the library's nodes).
@@ -425,12 +430,20 @@ def bates_temperature(z_km):
     return 1000.0 - 800.0 * np.exp(-0.02 * (z_km - 100.0))
 
 
-def bates_hydrostatic(r_m: np.ndarray, ref: Reference, p_points=16):
+def workload_gravity(r_m):
+    """Gravity of the shell workloads, g = 9.81 (R_E / r)^2 [m/s^2], r in m."""
+    return G_SURFACE * (R_EARTH / r_m) ** 2
+
+
+def bates_hydrostatic(r_m: np.ndarray, ref: Reference, p_points=16, temperature=None, gravity=None):
     """Density [kg/m^3] and temperature [K] of the Bates atmosphere in hydrostatic balance.
 
     ln p(r) = ln p0 - int_{R0}^{r} m g(s) / (k_B T(s)) ds with g = 9.81 (R_E/s)^2, integrated by
     composite Gauss-Legendre between consecutive distinct radii; rho = p m / (k_B T).
+    temperature(z_km) and gravity(r_m) default to the Bates profile and workload_gravity.
     """
+    temperature = temperature or bates_temperature
+    gravity = gravity or workload_gravity
     R0 = R_EARTH + 100.0e3
     m = ref.m_O
     shape = r_m.shape
@@ -441,10 +454,10 @@ def bates_hydrostatic(r_m: np.ndarray, ref: Reference, p_points=16):
     edges = np.concatenate([[R0], uniq])
     lo, hi = edges[:-1], edges[1:]
     s = 0.5 * (hi - lo)[:, None] * xg[None, :] + 0.5 * (hi + lo)[:, None]
-    integrand = m * G_SURFACE * (R_EARTH / s) ** 2 / (K_B * bates_temperature((s - R_EARTH) / 1.0e3))
+    integrand = m * gravity(s) / (K_B * temperature((s - R_EARTH) / 1.0e3))
     seg = 0.5 * (hi - lo) * (integrand @ wg)
     lnp_rel = -np.cumsum(seg)
-    T = bates_temperature((uniq - R_EARTH) / 1.0e3)
+    T = temperature((uniq - R_EARTH) / 1.0e3)
     p0 = ref.rho0 * K_B * ref.T0 / m
     rho = p0 * np.exp(lnp_rel) * m / (K_B * T)
     return rho[inv].reshape(shape), T[inv].reshape(shape)

@@ -103,7 +103,7 @@ def test_training_lowers_the_loss_and_cuts_gmres_iterations():
     network lowers its loss, converges where the untrained network does not, needs fewer GMRES
     iterations than unpreconditioned GMRES, and reaches the block-Jacobi step's state to the Newton
     tolerance. (Exact block-Jacobi needs about 10x fewer iterations still; at 60 s neither network
-    converges within GMRES(30) x 40 cycles — recorded in the design doc.)"""
+    converges within GMRES(30) x 40 cycles.)"""
     import torch
     from paper_2306_01085_gb300 import build as B
     from paper_2306_01085_gb300 import dg as DG

@@ -5,7 +5,8 @@ variable as max|x - x_ref| / max|x_ref| and held to 1e-4 (about 1700 eps_32). Tw
 factors multiply eps_32 = 2^-24: the cancellation between the volume, source and face terms of
 the residual (printed as kappa; up to ~220 where pressure balances gravity), and the rounding of
 the LDG gradient of a variable with a large mean (sqrt(rho) T), which grows like |u| / (h |grad u|)
-and feeds the heat flux. The measured values are recorded in the design doc.
+and feeds the heat flux. Measured on GB300: box residual <= 1.7e-5, Jv <= 2.4e-7; p = 3 shell
+residual <= 1.5e-5, Jv <= 6.6e-6.
 """
 import numpy as np
 import pytest

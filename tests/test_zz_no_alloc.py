@@ -34,14 +34,18 @@ def _rel_err(a, b):
     return np.abs(a - b).max(1) / np.abs(b).max(1)
 
 
-@pytest.mark.parametrize("name,p", [("box", 2), ("shell", 3)])
+@pytest.mark.parametrize("name,p", [("box", 2), ("shell", 3), ("box", 4), ("comp", 2)])
 def test_static_residual_matches_dg_residual_twice(env, name, p):
     """Two calls in a row (different states, so stale scratch from the first would show) agree
-    with dg_residual to 1e-12 per variable."""
+    with dg_residual to 1e-12 per variable: a periodic box at p = 2 and p = 4 (64 elements, under
+    the 335-element limit of p = 4), an EUV shell at p = 3, and a variable-composition shell whose
+    mixture fields reach the kernels through the mesh view."""
     torch, DG, L = env
     from paper_2306_01085_gb300 import workloads as W
     if name == "box":
         desc = W.box_desc(p=p, n=4)
+    elif name == "comp":
+        desc = W.shell_desc(n=2, nr=2, p=p, euvac=True, day=172.0, composition=True)
     else:
         desc = W.shell_desc(n=3, nr=2, p=p, euv=True)
     m = DG.Mesh(desc)
