@@ -52,7 +52,12 @@ def parse():
     ap.add_argument("--config", default=CONFIG_NAME)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-implicit", action="store_true", help="leave the implicit-step comparison off the line")
+    ap.add_argument("--implicit-config", default="shell32x16_p2_euv")
+    ap.add_argument("--implicit-chosen", default="mixed_bj16")
+    ap.add_argument("--implicit-steps", type=int, default=2)
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-procs", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--implicit", action="store_true",
                     help="time the implicit DIRK step variants instead (configs shell32x16_p2_euv, shell48x16_p3_euv)")
     ap.add_argument("--variants", default="plain_bj,mixed_bj,mixed_mlp,plain_none",
@@ -67,8 +72,12 @@ def parse():
 
 
 # ----------------------------------------------------------------------------------------------
-# oracle timing (cpu_baseline leg and --impl reference): the oracle as it stands, one thread
+# oracle timing (cpu_baseline leg and --impl reference): the oracle as it stands, on one thread and
+# on every host core (the sample's elements split across processes)
 # ----------------------------------------------------------------------------------------------
+SAMPLE_BLOCK = 4   # panel 0, 4 x 4 angular cells, all layers: 128 elements of the 12,288-element shell
+
+
 def oracle_sample(desc, block):
     """A contiguous block of elements (panel 0, block x block cells, all layers) of the shell, or
     the first block^2 * nz elements of a box."""
@@ -79,36 +88,99 @@ def oracle_sample(desc, block):
     return np.arange(min(desc.n_elem, block * block * desc.nz))
 
 
-def cpu_worker(config, steps, block):
-    """Time the oracle's residual + Jv on a sample of elements; prints JSON (runs in a child)."""
-    import numpy as np
-    from oracle import dg as OD
+def cpu_model():
+    """The host CPU's model name and its core count."""
+    name = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model"):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not name:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.split(":")[0].strip() in ("Model name", "Vendor ID"):
+                    name = ln.split(":", 1)[1].strip()
+                    if ln.startswith("Model name"):
+                        break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return name or "unknown", os.cpu_count() or 1
+
+
+_W = {}
+
+
+def _worker_init(config):
     from oracle import mesh as OM
     from paper_2306_01085_gb300 import workloads as W
     desc = W.CONFIGS[config][0]()
     om = OM.OracleMesh(desc)
-    u = W.state_for(desc, om.X, 2)
-    v = W.unit_vector(102, u.shape)
-    sample = oracle_sample(desc, block)
+    _W.update(om=om, u=W.state_for(desc, om.X, 2), v=W.unit_vector(102, (desc.n_elem, 5, om.Np)))
+
+
+def _worker_chunk(elems):
+    from oracle import dg as OD
+    OD.residual(_W["om"], _W["u"], None, 0.0, elems=elems)
+    OD.jvp(_W["om"], _W["u"], _W["v"], 0.0, elems=elems)
+    return len(elems)
+
+
+def cpu_worker(config, steps, block, procs):
+    """Time the oracle's residual + Jv on a sample of elements with `procs` processes (forked after
+    the mesh is built; this process never touches a GPU); prints JSON (runs in a child)."""
+    import multiprocessing as mp
+    import numpy as np
+    _worker_init(config)
+    desc_n = _W["om"].desc
+    sample = oracle_sample(desc_n, block)
+    chunks = [c for c in np.array_split(sample, procs) if len(c)]
     times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        OD.residual(om, u, None, 0.0, elems=sample)
-        OD.jvp(om, u, v, 0.0, elems=sample)
-        times.append(time.perf_counter() - t0)
-    dof = len(sample) * 5 * om.Np
-    print(json.dumps({"times": times, "dof": dof, "elements": int(len(sample))}))
+    if procs == 1:
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            _worker_chunk(sample)
+            times.append(time.perf_counter() - t0)
+    else:
+        with mp.get_context("fork").Pool(procs) as pool:
+            pool.map(_worker_chunk, chunks)              # warm the workers
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                pool.map(_worker_chunk, chunks)
+                times.append(time.perf_counter() - t0)
+    dof = len(sample) * 5 * _W["om"].Np
+    print(json.dumps({"times": times, "dof": dof, "elements": int(len(sample)), "procs": procs}))
 
 
-def run_cpu_worker(config, steps, block):
+def run_cpu_worker(config, steps, block, procs=1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", str(block), "--config", config,
-           "--steps", str(steps)]
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", str(block), "--cpu-procs", str(procs),
+           "--config", config, "--steps", str(steps)]
     res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     if res.returncode != 0:
         raise RuntimeError(res.stderr[-2000:])
     return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_leg(config, steps=2):
+    """The oracle on the same element sample on one thread and on every core: both values, the
+    cores used and the CPU model."""
+    model, ncpu = cpu_model()
+    one = run_cpu_worker(config, steps, SAMPLE_BLOCK, 1)
+    allc = run_cpu_worker(config, steps, SAMPLE_BLOCK, ncpu) if ncpu > 1 else one
+    v1 = one["dof"] / min(one["times"])
+    vn = allc["dof"] / min(allc["times"])
+    sample = (f"residual + complex-step Jv of {one['elements']} contiguous elements ({one['dof']} DOF; panel 0, "
+              f"{SAMPLE_BLOCK}x{SAMPLE_BLOCK} cells, all layers) of the same shell per step, best of {steps}")
+    return {"value": vn, "unit": UNIT, "cores": allc["procs"], "kind": "oracle", "sample": sample,
+            "one_thread": {"value": v1, "cores": 1}, "all_cores": {"value": vn, "cores": allc["procs"]},
+            "cpu_model": model, "nproc": ncpu}
 
 
 # ----------------------------------------------------------------------------------------------
@@ -128,7 +200,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
@@ -138,18 +210,27 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark(self):
+        """Index of the next sample (to summarise a part of the loaded window)."""
+        return len(self.lines)
+
     def stop(self):
         if not self.proc:
             return None
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.proc = None
+        return self.summary()
+
+    def summary(self, start=0, end=None):
+        """Median SM clock, max clock and throttle reasons of the samples [start, end)."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[start:end]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -164,14 +245,27 @@ class ClockSampler:
         if not sm:
             return None
         sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "interval_ms": 50}
 
 
 # ----------------------------------------------------------------------------------------------
-# FP64 work of the kernels: (2 DFMA + DMUL + DADD) per element from one ncu capture of each kernel
-# (profiles/fp64_residual_jv_shell16x8_p4.md); only valid for the kernels of that capture, so the
-# table is keyed by the source digest of the library it was measured on.
+# algorithmic work of the step's kernels
 # ----------------------------------------------------------------------------------------------
+# HBM bytes of the method per unknown for one fused residual + exact Jv in two passes, geometry
+# recomputed: pass 1 reads u, v and writes q, q_dot (8 + 8 + 24 + 24 B); pass 2 reads u, q, v, q_dot
+# and writes r, Jv (64 + 16 B).
+ALGO_BYTES_PER_DOF = 144
+
+# FP64 flops (value, exact tangent) of the pointwise physics of the shell16x8_p4 workload (mu, kappa
+# ~ T^0.69, no heating), counted on the oracle's own expressions with shared primitives:
+# tests/test_flop_counts.py recomputes these numbers. Transcendental calls (exp, pow) are listed
+# apart and not converted to flops.
+PHYS_FLOPS = {"volume_point": (262, 480), "face_interior": (437, 721), "face_wall": (225, 376),
+              "face_outflow": (143, 229)}
+PHYS_TRANSCENDENTALS = {"volume_point": 3, "face_interior": 8, "face_wall": 6, "face_outflow": 3}
+
+
 def grad_flops_per_element(N, NC=2):
     """FP64 flops of the sum-factorised LDG gradient (k_grad) per element, counted from the
     algorithm (an FMA is 2 flops): per component c, at each of the N^3 Gauss points G u (9),
@@ -182,15 +276,42 @@ def grad_flops_per_element(N, NC=2):
     return 5 * NC * (NP * (48 + 18 * N) + 6 * NF * (5 + 6 * N))
 
 
-# FP64 flops per element: k_grad from the algorithm; k_volume and k_faces (pointwise physics
-# dominated) as executed, (2 DFMA + DMUL + DADD) thread instructions of the ncu capture of the
-# residual kernels whose source digest is CAPTURE_DIGEST (profiles/fp64_residual_jv_shell16x8_p4.md)
-FP64_FLOPS_PER_ELEMENT = {("k_grad", 5): float(grad_flops_per_element(5)), ("k_volume", 5): 210000.0,
-                          ("k_faces", 5): 85028.1}
-FLOPS_KIND = {"k_grad": "algorithmic (sum-factorisation count)", "k_volume": "executed (ncu instruction counts)",
-              "k_faces": "executed (ncu instruction counts)"}
-DRAM_BYTES_PER_LAUNCH = {("k_grad", 5): 1206108672.0, ("k_volume", 5): 912022272.0, ("k_faces", 5): 755261952.0}
-CAPTURE_DIGEST = "a3a5ace70bb03005accaf9eafe37c37425512c87388f0f7d4384474e5ccbcaba"
+def kernel_flops(N, n_elem, n_interior, n_wall, n_outflow):
+    """Algorithmic FP64 flops per launch of each kernel of the fused residual + exact Jv (value and
+    tangent planes):
+      k_interp  3 passes of N-point contractions per Gauss point and one per face point, 5 variables;
+      k_grad    grad_flops_per_element;
+      k_volume  pointwise flux and source, plus per plane and Gauss point the reference fluxes
+                (15 x 3 FMA = 90), the source weighting (5), the weak derivative (5 x 3 x N FMA),
+                the face lifting (5 x 6 FMA = 60) and the projection B^T (5 x 3 x N FMA);
+      k_faces   the numerical flux of Eq. LDG2 per interior, wall and outflow face point."""
+    NP, NF = N ** 3, N ** 2
+    interp = 2 * 5 * (NP * 3 * 2 * N + 6 * NF * 2 * N)
+    volume = NP * (sum(PHYS_FLOPS["volume_point"]) + 2 * (155 + 60 * N))
+    faces = NF * (n_interior * sum(PHYS_FLOPS["face_interior"]) + n_wall * sum(PHYS_FLOPS["face_wall"])
+                  + n_outflow * sum(PHYS_FLOPS["face_outflow"]))
+    return {"k_interp": interp * n_elem, "k_grad": grad_flops_per_element(N) * n_elem,
+            "k_volume": volume * n_elem, "k_faces": faces}
+
+
+def face_kinds(desc):
+    """(interior, wall, outflow) faces of a workload mesh: 6 face slots per element, each interior
+    face shared by two elements; shells have 6 nx^2 faces on each sphere, boxes nx ny on each z end
+    unless z is periodic."""
+    E = desc.n_elem
+    nb = 6 * desc.nx * desc.nx if desc.kind == 1 else (desc.nx * desc.ny if desc.bc_lo else 0)
+    kinds = {0: 0, 1: 0, 2: 0}
+    if nb:
+        kinds[desc.bc_lo] += nb
+        kinds[desc.bc_hi] += nb
+    return 3 * E - nb, kinds[1], kinds[2]
+
+
+# DRAM bytes per launch of each kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the kernel sources whose digest is CAPTURE_DIGEST; on other sources the
+# traffic is reported as null.
+DRAM_BYTES_PER_LAUNCH = {}
+CAPTURE_DIGEST = None
 RESIDUAL_SOURCES = ("dg_kernels.cuh", "dg_internal.cuh", "dg_map.cuh", "dg_kernels_n5.cu")
 
 
@@ -221,6 +342,47 @@ def rank_aggregate(ms, n_dof, world, device="cuda"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     return ms_max, world * n_dof / (ms_max * 1e-3)
+
+
+def roofline_of(mesh, desc, config, prof, ms_step, f32):
+    """The step against the HBM roofline (the method's 144 B per unknown), with each kernel's
+    algorithmic FP64 work against the FP64 peak beside it."""
+    achieved = ALGO_BYTES_PER_DOF * mesh.n_dof / (ms_step * 1e-3) / 1e9
+    fresh = (not f32 and config == CONFIG_NAME and CAPTURE_DIGEST is not None
+             and residual_kernel_digest() == CAPTURE_DIGEST)
+    traffic = sum(DRAM_BYTES_PER_LAUNCH.values()) if fresh and DRAM_BYTES_PER_LAUNCH else None
+    total_ms = sum(v[0] for v in prof.values())
+    dom_name, (dom_ms, dom_cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    out = {"bound": "hbm", "scope": "the fused residual + exact Jv step (k_interp, k_grad, k_faces, k_volume)",
+           "achieved": round(achieved, 2), "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": round(achieved / HBM_PEAK_GBS, 5),
+           "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+           "bytes_per_dof": ALGO_BYTES_PER_DOF, "traffic": traffic,
+           "traffic_kind": "DRAM bytes per step, ncu dram__bytes_read.sum + dram__bytes_write.sum of these sources"
+           if traffic else None,
+           "dominant_kernel": {"name": dom_name, "launch_ms": round(dom_ms / dom_cnt, 4),
+                               "share": round(dom_ms / total_ms, 4)}}
+    if f32 or config != CONFIG_NAME:
+        return out
+    n_int, n_wall, n_out = face_kinds(desc)
+    flops = kernel_flops(desc.p + 1, mesh.n_elem, n_int, n_wall, n_out)
+    fp64 = {}
+    for k, fl in flops.items():
+        if k in prof:
+            ms_launch = prof[k][0] / prof[k][1]
+            tf = fl / (ms_launch * 1e-3) / 1e12
+            fp64[k] = {"flops_per_launch": fl, "launch_ms": round(ms_launch, 4), "tflops": round(tf, 4),
+                       "frac": round(tf / FP64_PEAK_TFLOPS, 4)}
+    step_flops = sum(flops.values())
+    out["fp64"] = {"peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                   "peak_kind": "FP64 from unit counts x max SM clock (2 DFMA/SM/cycle, 152 SMs, 2.07 GHz)",
+                   "peak_probe": round(float(__import__("paper_2306_01085_gb300.dg", fromlist=["x"]).probe_fp64()), 4),
+                   "flops_kind": "algorithmic: the oracle's pointwise expressions counted on an operation-"
+                                 "counting scalar (value + forward-mode tangent), transcendental calls not "
+                                 "included; sum-factorised contractions counted from the algorithm",
+                   "step_flops": step_flops, "step_tflops": round(step_flops / (ms_step * 1e-3) / 1e12, 4),
+                   "step_frac": round(step_flops / (ms_step * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                   "kernels": fp64}
+    return out
 
 
 def main_ours(args):
@@ -258,21 +420,24 @@ def main_ours(args):
         else:
             mesh.jvp(ug, vg, t=0.0, out=jv, r_out=r)
 
+    # clocks sampled every 50 ms over the whole loaded window (warm-up, timed steps, end-to-end leg
+    # and the implicit steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     if not (torch.isfinite(r).all() and torch.isfinite(jv).all()):
         raise RuntimeError("non-finite residual or Jv")
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     mesh.profile_start(capacity=64 * args.steps + 64)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    mark0 = clocks.mark()
     wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(k & 0xFF)                 # write 2x L2 between steps (outside the events)
@@ -281,39 +446,14 @@ def main_ours(args):
         ends[k].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    mark1 = clocks.mark()
     if world > 1:
         dist.barrier()
     prof, launches = mesh.profile_stop()
-    clk = clocks.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_mean = sum(ms) / len(ms)
     ms_max, value = rank_aggregate(ms_mean, mesh.n_dof, world)
-
-    # dominant kernel and its FP64 roofline
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_cnt) = dom
-    per_launch_ms = dom_ms / dom_cnt
-    key = (dom_name, desc.p + 1)
-    fpe = None if args.f32 else FP64_FLOPS_PER_ELEMENT.get(key)
-    flops = fpe * mesh.n_elem if fpe else None
-    achieved = flops / (per_launch_ms * 1e-3) / 1e12 if flops else None
-    probe = DG.probe_fp64()
-    fresh = residual_kernel_digest() == CAPTURE_DIGEST
-    traffic = DRAM_BYTES_PER_LAUNCH.get(key) if (args.config == CONFIG_NAME and fresh and not args.f32) else None
-    roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 4) if achieved else None,
-                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4) if achieved else None, "traffic": traffic,
-                "peak_kind": "FP64 from unit counts x max SM clock (2 DFMA/SM/cycle, 152 SMs, 2.07 GHz)",
-                "flops_kind": FLOPS_KIND.get(dom_name),
-                "peak_probe": round(probe, 4), "launch_ms": round(per_launch_ms, 4), "fp64_flops_per_launch": flops,
-                "share": round(dom_ms / sum(v[0] for v in prof.values()), 4),
-                "counters": "ncu capture of these kernel sources" if fresh else "ncu capture of earlier kernel sources (flops as then)",
-                "dram_gbs": round(traffic / (per_launch_ms * 1e-3) / 1e9, 1) if traffic else None}
-
-    # the whole step against HBM: the two-pass minimum of 144 B/DOF (u, v in; q, q_dot out; u, q,
-    # v, q_dot in; r, Jv out)
-    roofline["hbm_context"] = {"bytes_per_dof": 144, "achieved_gbs": round(144 * mesh.n_dof / (ms_max * 1e-3) / 1e9, 1),
-                               "peak_gbs": HBM_PEAK_GBS, "frac": round(144 * mesh.n_dof / (ms_max * 1e-3) / 1e9 / HBM_PEAK_GBS, 4)}
+    roofline = roofline_of(mesh, desc, args.config, prof, ms_max, args.f32)
 
     # end to end through the public API: every step copies its inputs from pinned host memory and
     # its results back to pinned host memory. The copies run on their own streams with two device
@@ -379,13 +519,21 @@ def main_ours(args):
         _, e2e_value = rank_aggregate(e2e_ms, mesh.n_dof, world)
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 2 * 8 * mesh.n_dof, "d2h_bytes_per_step": 2 * 8 * mesh.n_dof}
+    mesh.close()
+    del flush
+
+    # the implicit-step half of the metric: plain FP64 against the chosen mixed-precision variant
+    implicit = None
+    if not args.no_implicit and not args.f32:
+        implicit = implicit_variants(args.implicit_config, ["plain_bj", args.implicit_chosen],
+                                     args.implicit_steps, clocks=clocks)
+        implicit = implicit_summary(implicit, args.implicit_chosen)
+    clk_all = clocks.stop()
+    clk_timed = clocks.summary(mark0, mark1)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = run_cpu_worker(args.config, 1, 4)
-        cpu = {"value": res["dof"] / min(res["times"]), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"residual + complex-step Jv of {res['elements']} contiguous elements "
-                         f"({res['dof']} DOF; panel 0, 4x4 cells, all layers) of the same shell, one thread"}
+        cpu = cpu_baseline_leg(args.config)
 
     if world > 1:
         dist.barrier()
@@ -398,78 +546,72 @@ def main_ours(args):
                           "l2": "2x L2 buffer written between timed steps", "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                "kernels": {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items()},
-               "clocks": clk, "wall_s_timed": round(wall, 4)}
+               "clocks": clk_timed, "clocks_loaded_window": clk_all, "wall_s_timed": round(wall, 4),
+               "implicit": implicit}
         print(json.dumps(out), flush=True)
-    mesh.close()
     if world > 1:
         dist.destroy_process_group()
 
 
 def main_reference(args):
-    """The oracle (this repository's CPU reference of the method) on the same workload, one thread."""
+    """The oracle (this repository's CPU statement of the method) on the same workload: the element
+    sample of the cpu_baseline leg, split across every host core."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     sys.path.insert(0, ROOT)
     from paper_2306_01085_gb300 import workloads as W
-    res = run_cpu_worker(args.config, args.warmup + args.steps, 2)
+    model, ncpu = cpu_model()
+    res = run_cpu_worker(args.config, args.warmup + args.steps, SAMPLE_BLOCK, ncpu)
     times = res["times"][args.warmup:] or res["times"]
     ms = 1e3 * sum(times) / len(times)
     value = res["dof"] / (ms * 1e-3)
-    sample = (f"residual + complex-step Jv of {res['elements']} contiguous elements ({res['dof']} DOF) of the "
-              f"same shell per step, one thread")
+    sample = (f"residual + complex-step Jv of {res['elements']} contiguous elements ({res['dof']} DOF; panel 0, "
+              f"{SAMPLE_BLOCK}x{SAMPLE_BLOCK} cells, all layers) of the same shell per step, split across "
+              f"{res['procs']} processes")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"{args.config}: {W.CONFIGS[args.config][1]}"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["procs"], "kind": "oracle", "sample": sample,
+                            "cpu_model": model, "nproc": ncpu},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def main_implicit(args):
-    """Wall time per implicit DIRK(3,3) step of 60 s for the solver variants (1 GPU).
+IMPLICIT_VARIANTS = {
+    "plain_bj": dict(precond="bj", jv_prec="f64"),
+    "mixed_bj": dict(precond="bj", jv_prec="f32"),
+    "plain_none": dict(precond="none", jv_prec="f64"),
+    "mixed_mlp": dict(precond="mlp", jv_prec="f32"),
+    "mixed_rb_bj": dict(precond="rb_bj", jv_prec="f32"),
+    "mixed_rb": dict(precond="rb", jv_prec="f32"),
+    "mixed_bj16": dict(precond="bj16", jv_prec="f32"),
+}
 
-    plain_bj:   FP64 residual and exact FP64 Jv, block-Jacobi on exact blocks (FP32 LU)
-    mixed_bj:   FP64 residual, FP32 inner Jv and FP32-assembled blocks (FP32 LU)
-    plain_none: FP64 unpreconditioned GMRES(30)
-    mixed_mlp:  mixed precision with the learned diagonal + low-rank preconditioner, trained first on
-                the exact blocks of --mlp-steps plain steps (training time reported separately)
-    mixed_rb_bj: mixed precision, the reduced basis of the last 8 Newton updates (Sec. 3.2) over
-                block-Jacobi, with the RB initial guess
-    mixed_rb:   mixed precision, the reduced basis over the mass matrix (nothing assembled)
-    mixed_bj16: mixed_bj with the inverses stored as FP16 (power-of-two column scales)
-    Every variant starts from the same state; the final states are compared with plain_bj.
-    """
+
+def implicit_variants(config, names, n_steps, clocks=None, mlp_steps=2, mlp_epochs=20):
+    """Wall time per implicit DIRK(3,3) step of 60 s for the solver variants (1 GPU), every variant
+    from the same state; final states compared with plain_bj. With clocks (a running ClockSampler)
+    each variant's steps get their own clock summary."""
     import numpy as np
     import torch
     from paper_2306_01085_gb300 import build as B
     from paper_2306_01085_gb300 import dg as DG
     from paper_2306_01085_gb300 import workloads as W
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     B.build()
-    config = args.config if args.config != CONFIG_NAME else "shell32x16_p2_euv"
     desc = W.CONFIGS[config][0]()
     mesh = DG.Mesh(desc)
     u0 = torch.from_numpy(W.state_for(desc, mesh.nodes().cpu().numpy(), 2)).cuda()
     dt = 60.0 / W.shell_reference().t0
-    variants = {
-        "plain_bj": dict(precond="bj", jv_prec="f64"),
-        "mixed_bj": dict(precond="bj", jv_prec="f32"),
-        "plain_none": dict(precond="none", jv_prec="f64"),
-    }
-    variants["mixed_mlp"] = dict(precond="mlp", jv_prec="f32")
-    variants["mixed_rb_bj"] = dict(precond="rb_bj", jv_prec="f32")
-    variants["mixed_rb"] = dict(precond="rb", jv_prec="f32")
-    variants["mixed_bj16"] = dict(precond="bj16", jv_prec="f32")
     results, finals = {}, {}
     training = None
-    if "mixed_mlp" in args.variants.split(","):
+    if "mixed_mlp" in names:
         # harvest exact blocks from plain steps (each step's initial state, coefficient dt a_ii),
         # then train the network with the library's own kernels
         gamma = float(DG.dirk_tableau(3)[0][0, 0])
-        n_harvest = max(1, args.mlp_steps)
+        n_harvest = max(1, mlp_steps)
         mesh.mlp_init(hidden=256, rank=16, max_samples=n_harvest * mesh.n_elem, seed=11)
         u = u0.clone()
         t_h = time.perf_counter()
@@ -479,21 +621,22 @@ def main_implicit(args):
         t_h = time.perf_counter() - t_h
         torch.cuda.synchronize()
         t_t = time.perf_counter()
-        first, last = mesh.mlp_train(epochs=args.mlp_epochs, batch=1024, lr=1e-3)
+        first, last = mesh.mlp_train(epochs=mlp_epochs, batch=1024, lr=1e-3)
         torch.cuda.synchronize()
         training = {"samples": mesh.mlp_sizes()["n_samples"], "harvest_steps": n_harvest,
                     "harvest_s": round(t_h, 2), "train_s": round(time.perf_counter() - t_t, 2),
-                    "epochs": args.mlp_epochs, "loss_first_epoch": first, "loss_last_epoch": last,
+                    "epochs": mlp_epochs, "loss_first_epoch": first, "loss_last_epoch": last,
                     "params": mesh.mlp_sizes()["n_params"]}
-    for name in args.variants.split(","):
-        kw = variants[name]
+    for name in names:
+        kw = IMPLICIT_VARIANTS[name]
         u = u0.clone()
         mesh.rb_reset()
         steps = []
         rc = 0
         kernels = None
-        for k in range(args.steps):
-            last = k == args.steps - 1
+        mark = clocks.mark() if clocks else None
+        for k in range(n_steps):
+            last = k == n_steps - 1
             if last:
                 mesh.profile_start(capacity=200000)
             torch.cuda.synchronize()
@@ -516,22 +659,49 @@ def main_implicit(args):
                          "precond_s_per_step": [round(st["precond_ms"] / 1e3, 4) for st in steps],
                          "newton_per_step": newton, "gmres_per_step": gmres,
                          "gmres_per_newton": round(sum(gmres) / max(1, sum(newton)), 2),
-                         "kernels_last_step": kernels}
+                         "kernels_last_step": kernels,
+                         "clocks": clocks.summary(mark, clocks.mark()) if clocks else None}
     ref = finals.get("plain_bj")
     if ref is not None:
         du = np.abs(ref - u0.cpu().numpy()).max(axis=(0, 2))
         for name, fin in finals.items():
             if fin is not None and name != "plain_bj":
                 results[name]["final_diff_rel_to_change"] = (np.abs(fin - ref).max(axis=(0, 2)) / du).tolist()
+    out = {"metric": "implicit DIRK(3,3) step wall time at Newton 1e-8", "unit": "s/step",
+           "config": f"{config}: {W.CONFIGS[config][1]}", "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "dt_s": 60.0,
+           "steps": n_steps, "variants": results, "mlp_training": training}
     base = results.get("plain_bj", {}).get("wall_s_per_step")
-    out = {"metric": "implicit DIRK(3,3) step wall time at Newton 1e-8", "unit": "s/step", "config": config,
-           "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "dt_s": 60.0, "steps": args.steps, "variants": results,
-           "mlp_training": training}
-    for name in ("mixed_bj", "mixed_mlp", "mixed_rb_bj", "mixed_rb"):
-        if base and results.get(name, {}).get("rc") == 0:
+    for name in names:
+        if name != "plain_bj" and base and results.get(name, {}).get("rc") == 0:
             out[f"speedup_{name}_vs_plain_bj"] = round(np.mean(base) / np.mean(results[name]["wall_s_per_step"]), 3)
-    print(json.dumps(out), flush=True)
     mesh.close()
+    return out
+
+
+def implicit_summary(res, chosen):
+    """The implicit-step comparison as it goes on the benchmark line."""
+    v = res["variants"]
+    return {"metric": res["metric"], "unit": "s/step", "config": res["config"], "n_dof": res["n_dof"],
+            "dt_s": res["dt_s"], "steps": res["steps"], "newton_rtol": 1e-8, "chosen": chosen,
+            "chosen_means": "FP32 inner Jv and Gram-Schmidt arithmetic on the FP64 basis, exact element "
+                            "block-Jacobi with FP16-stored inverses; FP64 Newton residual",
+            "plain_means": "FP64 Jv and Gram-Schmidt, exact element block-Jacobi with FP32 inverses",
+            "speedup_chosen_vs_plain": res.get(f"speedup_{chosen}_vs_plain_bj"),
+            "variants": {k: {kk: vv for kk, vv in d.items() if kk != "kernels_last_step"} for k, d in v.items()}}
+
+
+def main_implicit(args):
+    """The implicit-step variants on one workload (--variants), one JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    config = args.config if args.config != CONFIG_NAME else args.implicit_config
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.2)
+    out = implicit_variants(config, args.variants.split(","), args.steps, clocks=clocks,
+                            mlp_steps=args.mlp_steps, mlp_epochs=args.mlp_epochs)
+    out["clocks_loaded_window"] = clocks.stop()
+    print(json.dumps(out), flush=True)
 
 
 def main_precision(args):
@@ -603,7 +773,7 @@ if __name__ == "__main__":
         main_precision(a)
         sys.exit(0)
     if a.cpu_worker:
-        cpu_worker(a.config, a.steps, a.cpu_worker)
+        cpu_worker(a.config, a.steps, a.cpu_worker, a.cpu_procs)
     elif a.impl == "reference":
         main_reference(a)
     else:

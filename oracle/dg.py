@@ -166,3 +166,12 @@ def mass_apply(mesh, v, elems=None):
     Wd = mesh.W[None, :] * mesh.detJ[elems]
     vG = np.einsum("gj,ecj->ecg", mesh.phi, v[elems])
     return np.einsum("eg,ecg,gi->eci", Wd, vG, mesh.phi)
+
+
+def mass_solve(mesh, v, elems=None):
+    """M^{-1} v on each element: a dense solve with the element mass matrix (phi_i, phi_j)."""
+    elems = np.arange(mesh.n_elem) if elems is None else np.asarray(elems)
+    Wd = mesh.W[None, :] * mesh.detJ[elems]
+    M = np.einsum("eg,gi,gj->eij", Wd, mesh.phi, mesh.phi)
+    b = v[elems].transpose(0, 2, 1)                                   # (e, i, c)
+    return np.ascontiguousarray(np.linalg.solve(M, b).transpose(0, 2, 1))

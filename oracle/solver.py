@@ -184,17 +184,19 @@ def jacobian_columns(mesh, U, t, h=1e-30):
     return J
 
 
-def diagonal_blocks(mesh, U, t, dt_aii):
+def diagonal_blocks(mesh, U, t, dt_aii, elems=None):
     """Exact element diagonal blocks of J_G = M - dt a_ii J_r: B[e] is (5 Np x 5 Np) in the
     element's [var][node] ordering. Column j of B[e] is (J_G e_{e,j}) restricted to element e,
-    computed on e and the elements its residual depends on."""
+    computed on e and the elements its residual depends on. elems: the blocks to build (all by
+    default); B[k] is then the block of elems[k]."""
     E, Np = mesh.n_elem, mesh.Np
     n = 5 * Np
-    B = np.zeros((E, n, n))
-    for e in range(E):
+    elems = list(range(E)) if elems is None else list(elems)
+    B = np.zeros((len(elems), n, n))
+    for k, e in enumerate(elems):
         for j in range(n):
             v = np.zeros_like(U)
             v[e].flat[j] = 1.0
             col = D.mass_apply(mesh, v, elems=[e])[0] - dt_aii * D.jvp(mesh, U, v, t, elems=[e])[0]
-            B[e][:, j] = col.ravel()
+            B[k][:, j] = col.ravel()
     return B

@@ -280,3 +280,17 @@ def test_free_stream_on_curved_shell():
         res.append(np.abs(r[interior]).max() / area)
     assert res[0] < 1e-13, res
     assert res[1] < 1e-5 and res[2] < 0.3 * res[1] and res[3] < 0.3 * res[2], res
+
+
+def test_mass_solve_inverts_mass_apply():
+    """M^{-1} (M x) = x and M (M^{-1} x) = x on a curved shell element set."""
+    from paper_2306_01085_gb300 import workloads as W2
+    from oracle import dg as OD2
+    from oracle import mesh as OM2
+    d = W2.shell_desc(n=1, nr=2, p=2)
+    om = OM2.OracleMesh(d)
+    x = W2.unit_vector(9, (om.n_elem, 5, om.Np))
+    a = OD2.mass_solve(om, OD2.mass_apply(om, x))
+    b = OD2.mass_apply(om, OD2.mass_solve(om, x))
+    assert np.abs(a - x).max() < 1e-12 * np.abs(x).max()
+    assert np.abs(b - x).max() < 1e-12 * np.abs(x).max()
