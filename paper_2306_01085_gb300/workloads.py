@@ -511,3 +511,122 @@ def state_for(desc: MeshDesc, x: np.ndarray, seed: int):
     if desc.kind == KIND_BOX:
         return box_state(x, seed)
     return shell_state(x, desc, seed)
+
+
+# ----------------------------------------------------------------------------------------------
+# radial 1D ensemble (Sec. 4.3: 28 elements, p = 2, first element 2.5 km, geometric growth, 100-600 km)
+# ----------------------------------------------------------------------------------------------
+@dataclass
+class RadialDesc:
+    """An ensemble of independent radial columns on one shared radial mesh.
+
+    Every column is the spherically symmetric thermosphere above one site (latitude, longitude) with
+    its own EUV heating efficiency epsilon and conductivity factor alpha0 (kappa_m = alpha0 x the
+    nominal law, Sec. 4.3); the physics numbers are those of the shell workloads (Sec. 2.4) with the
+    EUVAC heating of Sec. 2.2 (euv = EUV_EUVAC) or none (euv = 0)."""
+    p: int = 2
+    n_elem: int = 28
+    n_col: int = 1
+    r_inner: float = 0.0
+    r_outer: float = 0.0
+    h_first: float = 0.0
+    bc_lo: int = BC_WALL
+    bc_hi: int = BC_OUTFLOW
+    gamma: float = GAMMA
+    grashof: float = 100.0 ** 2 / GAMMA
+    prandtl: float = 0.7
+    mass: float = 1.0
+    visc_exp: float = 0.69
+    lambda0: float = 1.0
+    t_wall: float = 1.0
+    g_r0: float = 0.0
+    euv: int = EUV_EUVAC
+    euv_omega_t: float = 0.0
+    euv_day: float = 80.0
+    euv_f107: float = 150.0
+    euv_f107a: float = 150.0
+    euv_eff: float = 0.25        # the nominal efficiency; a column's own epsilon replaces it
+    euv_dsun: float = 1.0
+    ref_T0: float = 0.0
+    ref_rho0: float = 0.0
+    ref_m: float = 0.0
+    ref_g0: float = 0.0
+
+    @property
+    def n_node(self) -> int:
+        return self.n_elem * (self.p + 1)
+
+    @property
+    def n_dof_col(self) -> int:
+        return 3 * self.n_node
+
+    @property
+    def n_dof(self) -> int:
+        return self.n_col * self.n_dof_col
+
+
+def radial_desc(n_col=1, n_elem=28, p=2, h_first_km=2.5, euvac=True, ref: Reference | None = None,
+                day=80.0, f107=150.0, f107a=150.0) -> RadialDesc:
+    """The radial column mesh of the paper's 1D model: n_elem layers from 100 to 600 km with a first
+    layer of h_first_km and geometric growth (Sec. 3.3 / 4.3)."""
+    ref = ref or shell_reference()
+    H0 = ref.H0
+    r_in = (R_EARTH + 100.0e3) / H0
+    return RadialDesc(p=p, n_elem=n_elem, n_col=n_col, r_inner=r_in, r_outer=(R_EARTH + 600.0e3) / H0,
+                      h_first=h_first_km * 1.0e3 / H0, grashof=ref.Gr, prandtl=ref.Pr, g_r0=r_in,
+                      euv=EUV_EUVAC if euvac else 0, euv_omega_t=OMEGA_EARTH * ref.t0, euv_day=day,
+                      euv_f107=f107, euv_f107a=f107a, ref_T0=ref.T0, ref_rho0=ref.rho0, ref_m=ref.m_O,
+                      ref_g0=ref.g0)
+
+
+# the paper's parameter values (Sec. 4.3): epsilon and alpha0 grids
+RADIAL_EPS = (0.2, 0.225, 0.25, 0.275, 0.3)
+RADIAL_ALPHA0 = (0.5, 0.625, 0.75, 0.875, 1.0)
+
+
+def radial_params(n_col: int, seed: int = 21) -> np.ndarray:
+    """Per-column parameters [n_col][4] = (epsilon, alpha0, latitude, longitude) [-, -, rad, rad]:
+    the 25 (epsilon, alpha0) pairs of the paper's grids in turn, at seeded sites uniform on the
+    sphere (latitude asin(U(-1, 1)), longitude U(-pi, pi))."""
+    k = np.arange(n_col)
+    eps = np.array(RADIAL_EPS)[k % 5]
+    alpha = np.array(RADIAL_ALPHA0)[(k // 5) % 5]
+    u = uniform01(seed, 2 * n_col)
+    lat = np.arcsin(2.0 * u[:n_col] - 1.0)
+    lon = np.pi * (2.0 * u[n_col:] - 1.0)
+    return np.stack([eps, alpha, lat, lon], axis=1)
+
+
+def radial_nodes(desc: RadialDesc) -> np.ndarray:
+    """Radii [n_elem][p+1] of the GLL nodes of the radial mesh (the layers of radial_layers)."""
+    rl = radial_layers(desc.r_inner, desc.r_outer, desc.n_elem, desc.h_first)
+    s = 0.5 * (1.0 + gll_points(desc.p + 1))
+    return rl[:-1, None] + s[None, :] * (rl[1:] - rl[:-1])[:, None]
+
+
+def radial_state(desc: RadialDesc, seed: int = 3, ref: Reference | None = None, t_amp=0.01, v_ms=5.0):
+    """u [3][n_elem][p+1][n_col] = (log rho*, sqrt(rho*) v*, sqrt(rho*) T*) at the nodes: the Bates
+    atmosphere in hydrostatic balance, T x (1 + t_amp f), radial wind v_ms f' [m/s], with f, f' seeded
+    smooth profiles per column (sums of 4 sine modes of the height, amplitude 1)."""
+    ref = ref or shell_reference()
+    r = radial_nodes(desc)                                      # (E, N)
+    rho_d, T_d = bates_hydrostatic(r * ref.H0, ref)
+    s = (r - desc.r_inner) / (desc.r_outer - desc.r_inner)
+    ab = 2.0 * uniform01(seed, 16 * desc.n_col).reshape(desc.n_col, 2, 4, 2) - 1.0
+    modes = np.arange(1, 5)
+
+    def profile(c, k):
+        f = (ab[c, k, :, 0, None, None] * np.sin(np.pi * modes[:, None, None] * s[None])
+             + ab[c, k, :, 1, None, None] * np.cos(np.pi * modes[:, None, None] * s[None])).sum(0)
+        return f / max(1e-300, np.abs(f).max())
+
+    u = np.zeros((3,) + r.shape + (desc.n_col,))
+    for c in range(desc.n_col):
+        T = T_d / ref.T0 * (1.0 + t_amp * profile(c, 0))
+        v = v_ms / ref.a0 * profile(c, 1)
+        rho = rho_d / ref.rho0
+        sr = np.sqrt(rho)
+        u[0, :, :, c] = np.log(rho)
+        u[1, :, :, c] = sr * v
+        u[2, :, :, c] = sr * T
+    return u
