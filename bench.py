@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-implicit", action="store_true", help="leave the implicit-step comparison off the line")
+    ap.add_argument("--no-radial", action="store_true", help="leave the radial 1D ensemble off the line")
+    ap.add_argument("--radial", action="store_true", help="time the radial 1D ensemble alone")
+    ap.add_argument("--radial-columns", type=int, default=16384)
     ap.add_argument("--implicit-config", default="shell32x16_p2_euv")
     ap.add_argument("--implicit-chosen", default="mixed_bj16")
     ap.add_argument("--implicit-steps", type=int, default=2)
@@ -522,6 +525,11 @@ def main_ours(args):
     mesh.close()
     del flush
 
+    # the radial 1D ensemble (Sec. 4.3)
+    radial = None
+    if not args.no_radial and not args.f32:
+        radial = radial_leg(clocks=clocks)
+
     # the implicit-step half of the metric: plain FP64 against the chosen mixed-precision variant
     implicit = None
     if not args.no_implicit and not args.f32:
@@ -547,7 +555,7 @@ def main_ours(args):
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                "kernels": {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items()},
                "clocks": clk_timed, "clocks_loaded_window": clk_all, "wall_s_timed": round(wall, 4),
-               "implicit": implicit}
+               "implicit": implicit, "radial": radial}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -704,6 +712,93 @@ def main_implicit(args):
     print(json.dumps(out), flush=True)
 
 
+RADIAL_COLUMNS = 16384
+
+
+def radial_leg(n_col=RADIAL_COLUMNS, steps=20, warmup=3, implicit_steps=3, clocks=None):
+    """The radial 1D ensemble (Sec. 4.3's 28-element p = 2 column, DIRK(2,2) at 30 s) on one GPU:
+    n_col independent columns, each with its own site, EUV efficiency and conductivity factor.
+    Times the fused residual + exact Jv of the whole ensemble (2x L2 written between steps) and
+    whole DIRK(2,2) steps; reports DOF/s and column-steps/s."""
+    import numpy as np
+    import torch
+    from paper_2306_01085_gb300 import dg as DG
+    from paper_2306_01085_gb300 import workloads as W
+    d = W.radial_desc(n_col=n_col)
+    params = W.radial_params(n_col)
+    rad = DG.Radial(d, params)
+    u0 = W.radial_state(d, seed=3)
+    ug = torch.from_numpy(u0).cuda()
+    vg = torch.from_numpy(W.unit_vector(17, u0.shape)).cuda()
+    r, jv = rad.empty(), rad.empty()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        rad.jvp(ug, vg, 0.0, out=jv, r_out=r)
+    torch.cuda.synchronize()
+    mark = clocks.mark() if clocks else None
+    rad.profile_start(64 * steps + 64)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        rad.jvp(ug, vg, 0.0, out=jv, r_out=r)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    prof, launches = rad.profile_stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    if not (torch.isfinite(r).all() and torch.isfinite(jv).all()):
+        raise RuntimeError("non-finite radial residual or Jv")
+    clk_rj = clocks.summary(mark, clocks.mark()) if clocks else None
+    # implicit steps (each a whole DIRK(2,2) step of every column, host-synchronised Newton)
+    dt = 30.0 / W.shell_reference().t0
+    u = ug.clone()
+    rad.step(u, 0.0, dt, stages=2)                      # warm-up step (first-call costs)
+    torch.cuda.synchronize()
+    mark = clocks.mark() if clocks else None
+    rad.profile_start(100000)
+    walls, newton = [], []
+    for k in range(implicit_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = rad.step(u, (k + 1) * dt, dt, stages=2, newton_rtol=1e-8)
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - t0)
+        newton.append(st["newton"][:2])
+    sprof, slaunch = rad.profile_stop()
+    clk_st = clocks.summary(mark, clocks.mark()) if clocks else None
+    rad.close()
+    step_s = float(np.mean(walls))
+    n_dof = d.n_dof
+    return {"workload": f"radial1d_p2: {n_col} columns x 28 elements, p = 2 (the paper's 1D mesh: first layer "
+                        f"2.5 km, geometric growth, 100-600 km), EUVAC heating, 25 (epsilon, alpha0) pairs at "
+                        f"seeded sites", "n_col": n_col, "n_dof": n_dof, "dtype": "f64",
+            "residual_jv": {"metric": "DG residual+Jv DOFs/s", "value": n_dof / (ms * 1e-3), "unit": "DOF/s",
+                            "ms_per_step": round(ms, 4), "steps": steps, "warmup": warmup,
+                            "l2": "2x L2 buffer written between timed steps",
+                            "kernels": {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items()},
+                            "gpu_launches": launches, "clocks": clk_rj},
+            "implicit": {"metric": "DIRK(2,2) column-steps/s at Newton 1e-8 (dt = 30 s)",
+                         "value": n_col / step_s, "unit": "column-steps/s", "s_per_step": round(step_s, 5),
+                         "steps": implicit_steps, "newton_per_stage": newton,
+                         "jacobian": "FP32, colored tangent probing, banded LU per column; Newton on the FP64 residual",
+                         "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in sprof.items()},
+                         "gpu_launches": slaunch, "clocks": clk_st}}
+
+
+def main_radial(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2306_01085_gb300 import build as B
+    B.build()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.2)
+    out = radial_leg(n_col=args.radial_columns, steps=args.steps, warmup=args.warmup, clocks=clocks)
+    out["clocks_loaded_window"] = clocks.stop()
+    print(json.dumps(out), flush=True)
+
+
 def main_precision(args):
     """Precision study of the basis contractions on one GPU: the fused residual + exact Jv with the
     contractions in FP32, bfloat16 and binary16 operands (FP32 accumulation), and their hi + lo
@@ -771,6 +866,9 @@ if __name__ == "__main__":
         sys.exit(0)
     if a.precision:
         main_precision(a)
+        sys.exit(0)
+    if a.radial:
+        main_radial(a)
         sys.exit(0)
     if a.cpu_worker:
         cpu_worker(a.config, a.steps, a.cpu_worker, a.cpu_procs)

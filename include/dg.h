@@ -402,6 +402,81 @@ int dg_profile_start(dg_mesh* mesh, int32_t capacity);
 int dg_profile_stop(dg_mesh* mesh, int32_t n_kinds, double* ms, int32_t* count, int64_t* total);
 const char* dg_kernel_name(int32_t kind);
 
+/* ----------------------------------------------------------------------------------------------
+ * Radial 1D ensemble (Sec. 4.3: the radial one-dimensional model, run for parametric studies).
+ * The paper does not print the 1D equations; the library takes the spherically symmetric restriction
+ * of the 3D problem: fields of r only, radial velocity, u = (varrho, sqrt(rho) v_r, sqrt(rho) T); the
+ * LDG weak form of Eq. DGformulation with trial and test functions restricted to symmetric fields and
+ * the measure r^2 dr, so that the gradient of the radial velocity has a tangential part v/r and the
+ * momentum residual gains the tangential stress 2 F_tt / r; Eq. fluxSWNondimensional without the
+ * rotating-frame terms (not spherically symmetric); radial gravity; mu* = T*^visc_exp and
+ * kappa* = alpha0 T*^visc_exp (the conductivity factor of Sec. 4.3); EUVAC heating (DG_EUV_EUVAC,
+ * oxygen absorber) above the column's site with the column's efficiency epsilon; wall / outflow
+ * boundaries and the numerical flux of Eq. LDG2; (p+1)-point Gauss quadrature including the r^2.
+ * All columns share one radial mesh and the physics numbers; each has its own
+ * (epsilon, alpha0, latitude, longitude).
+ * Layout of u, r, v, jv (device, FP64): [3][n_elem][p+1][n_col] with the column index fastest
+ * (consecutive columns adjacent, so one thread per column reads coalesced), nodal GLL values.
+ * -------------------------------------------------------------------------------------------- */
+typedef struct dg_radial_desc {
+    int32_t p;            /* degree, 1..4 */
+    int32_t n_elem;       /* radial elements (shared by every column) */
+    int32_t n_col;        /* columns of the ensemble */
+    int32_t euv;          /* 0 (no heating) or DG_EUV_EUVAC */
+    int32_t bc_lo, bc_hi; /* DG_BC_WALL or DG_BC_OUTFLOW at the inner / outer radius */
+    double r_inner, r_outer, h_first;  /* radii and first-layer height (<= 0: uniform layers) */
+    double gamma, grashof, prandtl, mass, visc_exp, lambda0, t_wall;   /* as in dg_mesh_desc */
+    double g_r0;          /* g* = -(g_r0/r)^2 r_hat; also the Earth radius of the shadow test */
+    double euv_omega_t, euv_day, euv_f107, euv_f107a, euv_dsun;        /* as in dg_mesh_desc */
+    double ref_T0, ref_rho0, ref_m, ref_g0;
+} dg_radial_desc;
+
+typedef struct dg_radial dg_radial;
+
+typedef struct dg_radial_stats {
+    int32_t status;            /* the call's return code */
+    int32_t newton_iters[3];   /* Newton iterations per stage (the most any column needed) */
+    double max_ratio;          /* largest ||G||_2 / ||G(U^0)||_2 over columns at the end of the last stage */
+    double wall_ms;            /* host wall time of the call */
+} dg_radial_stats;
+
+/* Build the ensemble on the current device. node_r: optional HOST array [n_elem][p+1] of the node
+ * radii (NULL: geometric layers from desc); params: HOST array [n_col][4] = (epsilon, alpha0,
+ * latitude, longitude [rad]), read during the call. Allocates the library storage (synchronises).
+ * Errors: DG_EINVAL (sizes, p, boundaries, non-positive radii or alpha0), DG_ENOMEM, DG_ECUDA. */
+int dg_radial_create(const dg_radial_desc* desc, const double* node_r, const double* params, dg_radial** out);
+void dg_radial_destroy(dg_radial* rad);
+
+/* Residual r = (F_r, w')_{r^2} + (S, w)_{r^2} - [r^2 F_hat w] of every column at time t (FP64,
+ * stream-ordered). r must not overlap u. */
+int dg_radial_residual(dg_radial* rad, const double* u, double t, double* r, void* stream);
+
+/* Exact Jacobian-vector product J v of every column (forward-mode tangent, FP64); r_out (may be
+ * NULL) receives r(u) from the same pass. jv must not overlap u, v or r_out. */
+int dg_radial_jvp(dg_radial* rad, const double* u, const double* v, double t, double* jv, double* r_out,
+                  void* stream);
+
+/* One DIRK step (stages 1, 2 = DIRK(2,2), 3 = DIRK(3,3); the tableaux of dg_dirk_tableau) of
+ * M du/dt = r(u) for every column, in place on u. Each stage solves G(U) = 0 by a Newton iteration
+ * on the FP64 residual whose linear systems use the column's exact stage Jacobian
+ * J_G = M - dt a_ii J_r at the stage's first iterate, assembled in FP32 by colored tangent probing
+ * and factored by FP32 banded LU with partial pivoting (one thread per column); every column
+ * iterates until max over columns of ||G||_2 / ||G(U^0)||_2 <= newton_rtol or
+ * ||G||_2 <= 1e-14 ||M U||_2. Synchronises the stream (the host reads the largest ratio after every
+ * iteration). stats may be NULL. Errors: DG_ENOTCONV after max_newton iterations of a stage,
+ * DG_ENAN (non-finite norm or zero pivot), DG_EINVAL, DG_ENOMEM, DG_ECUDA; on an error u is left
+ * unchanged. */
+int dg_radial_step(dg_radial* rad, double* u, double t, double dt, int32_t stages, double newton_rtol,
+                   int32_t max_newton, dg_radial_stats* stats, void* stream);
+
+/* Sizes: columns, nodes per column (n_elem (p+1)), unknowns (3 n_col n_node). */
+int dg_radial_sizes(const dg_radial* rad, int64_t* n_col, int32_t* n_node, int64_t* n_dof);
+
+/* Tracing of the radial kernels, as dg_profile_start / dg_profile_stop for a mesh. */
+int dg_radial_profile_start(dg_radial* rad, int32_t capacity);
+int dg_radial_profile_stop(dg_radial* rad, int32_t n_kinds, double* ms, int32_t* count, int64_t* total);
+const char* dg_radial_kernel_name(int32_t kind);
+
 /*
  * FP64 throughput probe (the ceiling of the FP64 path, which is FP64-pipe bound on this part):
  * a fused multiply-add loop over 8 independent chains per thread on every SM, timed with CUDA

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/dg.h"
 
@@ -150,6 +151,12 @@ void dg_mlp_release(dg_mesh* m);
 
 namespace dg {
 int ensure_f32(dg_mesh* m);       // allocate and fill the FP32 workspace and geometry
+// EUVAC band coefficients, Sun declination and Chapman constants of a description (false if the
+// reference values needed are missing)
+bool euvac_coefficients(const dg_mesh_desc& d, Phys& P);
+// layer interfaces r_0 = r_in < ... < r_nz = r_out with heights h1 q^k (q solved by bisection so the
+// layers fill the shell; h1 <= 0: uniform layers), Sec. 3.3
+std::vector<double> radial_layers(double r_in, double r_out, int nz, double h1);
 // device address of dg_residual_static's scratch array on the current device dev (looked up once
 // per device; the lookup loads the module that holds the array)
 int static_scratch_address(int dev, double** out);

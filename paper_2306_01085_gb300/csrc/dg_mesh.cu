@@ -55,7 +55,7 @@ static int drv_mass_inv(dg_mesh* m, const double* v, double* mv, cudaStream_t s)
 // (or 1/m* for the single constituent), so with Phi_j = sum_s w_s phi_s^j and H = H0 H*,
 // q* = q H0/(rho0 c_v0 T0 a0) = e^varrho sum_j B_j Phi_j exp(-tau_j), tau_j = cc e^varrho Phi_j H* Ch,
 // B_j = eps I0_j (h c/lambda_j) H0 / (m0 c_v0 T0 a0) and cc = rho0 H0 / m0.
-static bool euvac_coefficients(const dg_mesh_desc& d, Phys& P) {
+bool euvac_coefficients(const dg_mesh_desc& d, Phys& P) {
   if (!(d.ref_T0 > 0 && d.ref_rho0 > 0 && d.ref_m > 0 && d.ref_g0 > 0 && d.euv_dsun > 0 && d.g_r0 > 0 &&
         d.mass > 0 && d.gamma > 1))
     return false;
@@ -86,7 +86,7 @@ static bool euvac_coefficients(const dg_mesh_desc& d, Phys& P) {
   return true;
 }
 
-static std::vector<double> radial_layers(double r_in, double r_out, int nz, double h1) {
+std::vector<double> radial_layers(double r_in, double r_out, int nz, double h1) {
   std::vector<double> r(nz + 1);
   const double total = r_out - r_in;
   if (h1 <= 0.0 || nz == 1) {

@@ -461,3 +461,134 @@ def _mesh_rb_reset(self):
 Mesh.rb_load = _mesh_rb_load
 Mesh.rb_initial_guess = _mesh_rb_initial_guess
 Mesh.rb_reset = _mesh_rb_reset
+
+
+# ----------------------------------------------------------------------------------------------
+# radial 1D ensemble (dg_radial_* in include/dg.h)
+# ----------------------------------------------------------------------------------------------
+class DgRadialDesc(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_int32), ("n_elem", ctypes.c_int32), ("n_col", ctypes.c_int32), ("euv", ctypes.c_int32),
+        ("bc_lo", ctypes.c_int32), ("bc_hi", ctypes.c_int32),
+        ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("h_first", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("grashof", ctypes.c_double), ("prandtl", ctypes.c_double),
+        ("mass", ctypes.c_double), ("visc_exp", ctypes.c_double), ("lambda0", ctypes.c_double),
+        ("t_wall", ctypes.c_double), ("g_r0", ctypes.c_double),
+        ("euv_omega_t", ctypes.c_double), ("euv_day", ctypes.c_double), ("euv_f107", ctypes.c_double),
+        ("euv_f107a", ctypes.c_double), ("euv_dsun", ctypes.c_double),
+        ("ref_T0", ctypes.c_double), ("ref_rho0", ctypes.c_double), ("ref_m", ctypes.c_double),
+        ("ref_g0", ctypes.c_double),
+    ]
+
+
+class DgRadialStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32 * 3), ("max_ratio", ctypes.c_double),
+                ("wall_ms", ctypes.c_double)]
+
+
+def _radial_lib():
+    L = lib()
+    if getattr(L, "_radial_ready", False):
+        return L
+    vp, dp, i32, d = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.dg_radial_create.argtypes = [ctypes.POINTER(DgRadialDesc), vp, vp, ctypes.POINTER(vp)]
+    L.dg_radial_destroy.argtypes = [vp]
+    L.dg_radial_destroy.restype = None
+    L.dg_radial_sizes.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_int32), i64p]
+    L.dg_radial_residual.argtypes = [vp, dp, d, dp, vp]
+    L.dg_radial_jvp.argtypes = [vp, dp, dp, d, dp, dp, vp]
+    L.dg_radial_step.argtypes = [vp, dp, d, d, i32, d, i32, ctypes.POINTER(DgRadialStats), vp]
+    L.dg_radial_profile_start.argtypes = [vp, i32]
+    L.dg_radial_profile_stop.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                         i64p]
+    L.dg_radial_kernel_name.argtypes = [i32]
+    L.dg_radial_kernel_name.restype = ctypes.c_char_p
+    L._radial_ready = True
+    return L
+
+
+class Radial:
+    """A library radial ensemble: n_col independent columns on one radial mesh (current device).
+    State tensors are float64 [3][n_elem][p+1][n_col] (column index fastest)."""
+
+    def __init__(self, desc: W.RadialDesc, params, node_r=None):
+        """params: numpy [n_col][4] = (epsilon, alpha0, latitude, longitude); node_r: optional numpy
+        [n_elem][p+1] node radii (None: the library's geometric layers)."""
+        import numpy as np
+        L = _radial_lib()
+        self.desc = desc
+        c = DgRadialDesc()
+        for name, _ in DgRadialDesc._fields_:
+            setattr(c, name, getattr(desc, name))
+        self._c = c
+        prm = np.ascontiguousarray(params, dtype=np.float64)
+        if prm.shape != (desc.n_col, 4):
+            raise DgError(f"params has shape {prm.shape}, expected {(desc.n_col, 4)}")
+        nr = None
+        if node_r is not None:
+            nr = np.ascontiguousarray(node_r, dtype=np.float64)
+            if nr.shape != (desc.n_elem, desc.p + 1):
+                raise DgError(f"node_r has shape {nr.shape}, expected {(desc.n_elem, desc.p + 1)}")
+        h = ctypes.c_void_p()
+        _check(L.dg_radial_create(ctypes.byref(c), None if nr is None else ctypes.c_void_p(nr.ctypes.data),
+                                  ctypes.c_void_p(prm.ctypes.data), ctypes.byref(h)))
+        self._h = h
+        nc, nn, nd = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        _check(L.dg_radial_sizes(h, ctypes.byref(nc), ctypes.byref(nn), ctypes.byref(nd)))
+        self.n_col, self.n_node, self.n_dof = nc.value, nn.value, nd.value
+        self.u_shape = (3, desc.n_elem, desc.p + 1, self.n_col)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _radial_lib().dg_radial_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self):
+        import torch
+        return torch.empty(self.u_shape, dtype=torch.float64, device="cuda")
+
+    def residual(self, u, t=0.0, out=None):
+        out = self.empty() if out is None else out
+        _check(_radial_lib().dg_radial_residual(self._h, _ptr(u, self.u_shape, "u"), float(t),
+                                                _ptr(out, self.u_shape, "r"), _stream()))
+        return out
+
+    def jvp(self, u, v, t=0.0, out=None, r_out=None):
+        out = self.empty() if out is None else out
+        _check(_radial_lib().dg_radial_jvp(self._h, _ptr(u, self.u_shape, "u"), _ptr(v, self.u_shape, "v"), float(t),
+                                           _ptr(out, self.u_shape, "jv"),
+                                           None if r_out is None else _ptr(r_out, self.u_shape, "r_out"), _stream()))
+        return out
+
+    def step(self, u, t, dt, stages=2, newton_rtol=1e-8, max_newton=20, check=True):
+        """One DIRK step in place on u; returns the statistics (raises on failure when check)."""
+        st = DgRadialStats()
+        rc = _radial_lib().dg_radial_step(self._h, _ptr(u, self.u_shape, "u"), float(t), float(dt), int(stages),
+                                          float(newton_rtol), int(max_newton), ctypes.byref(st), _stream())
+        if check:
+            _check(rc)
+        return {"rc": rc, "status": st.status, "newton": list(st.newton_iters), "max_ratio": st.max_ratio,
+                "wall_ms": st.wall_ms}
+
+    def profile_start(self, capacity=4096):
+        _check(_radial_lib().dg_radial_profile_start(self._h, capacity))
+
+    def profile_stop(self, n_kinds=16):
+        L = _radial_lib()
+        ms = (ctypes.c_double * n_kinds)()
+        cnt = (ctypes.c_int32 * n_kinds)()
+        tot = ctypes.c_int64()
+        _check(L.dg_radial_profile_stop(self._h, n_kinds, ms, cnt, ctypes.byref(tot)))
+        out = {}
+        for k in range(n_kinds):
+            name = L.dg_radial_kernel_name(k).decode()
+            if name and cnt[k]:
+                out[name] = (ms[k], cnt[k])
+        return out, tot.value
