@@ -637,6 +637,173 @@ __global__ void __launch_bounds__(NT) k_gj_inverse_cluster(long long E, int n, i
   cl.sync();
 }
 
+// Blocked Gauss-Jordan inversion on a thread-block cluster (blocks too large for one CTA's shared
+// memory). CTA `rank` keeps columns [rank w, rank w + w) in shared memory (column stride ld = n | 1,
+// odd, so row-wise and column-wise accesses are both free of bank conflicts). The columns are
+// processed in panels of at most B that never straddle two CTAs:
+//   1. the owner of the panel runs the unblocked in-place steps (pivot search over the rows below,
+//      row interchange, scaling, elimination) on the panel's columns only, with one thread per
+//      row and block-level barriers; the panel then holds the columns of the panel's transform
+//      T = G_b P_b ... G_1 P_1, which is the identity outside the panel's columns;
+//   2. one cluster barrier;
+//   3. every CTA applies T to each of its other columns x: the panel's row interchanges, then
+//      x <- x~ + P x_K, with x_K the panel rows of x, x~ = x with those rows zeroed and P the panel
+//      (read from the owner's shared memory through the cluster): a rank-b product, one thread per
+//      row accumulating over b with the panel row in registers.
+// One cluster barrier per panel replaces one per column. The panel's pivots are kept in two buffers
+// used in turn (a CTA may still read panel t's while the owner of panel t + 1 records its own).
+// After the last panel the columns are interchanged back in reverse pivot order as each CTA writes
+// them out. NT >= n threads (one row each).
+template <int NT, int B>
+__global__ void __launch_bounds__(NT) k_gj_blocked(long long E, int n, int w, float* __restrict__ blocks,
+                                                    int* __restrict__ piv, int* __restrict__ info) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const long long e = blockIdx.x / CL;
+  const int ld = n | 1;
+  extern __shared__ float sgb[];
+  float* A = sgb;                               // [w][ld] own columns
+  float* U = A + (size_t)w * ld;                // [B][w] panel rows of the own columns
+  float* r = U + (size_t)B * w;                 // [B] scaled pivot row of the panel
+  int* pp = reinterpret_cast<int*>(r + B);      // [2][B] the panel's pivot rows
+  int* pv = pp + 2 * B;                         // [n] every pivot row
+  int* cur = pv + n;
+  int* dest = cur + n;
+  constexpr int NWARP = NT / 32;
+  __shared__ float wval[NWARP];
+  __shared__ int widx[NWARP];
+  __shared__ int sp;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int j0 = rank * w;
+  const int nw = max(0, min(n, j0 + w) - j0);
+  float* Ag = blocks + e * (long long)n * n;
+  for (long long q = t; q < (long long)nw * n; q += NT) A[(q / n) * ld + q % n] = Ag[(long long)j0 * n + q];
+  cl.sync();
+  int panel = 0;
+  for (int k0 = 0; k0 < n; ++panel) {
+    const int owner = k0 / w;
+    const int kend = min(min(k0 + B, (owner + 1) * w), n);
+    const int b = kend - k0;
+    int* ppb = pp + (panel & 1) * B;
+    if (rank == owner) {
+      float* Pc = A + (size_t)(k0 - j0) * ld;   // the panel's first column
+      for (int c = 0; c < b; ++c) {
+        const int kc = k0 + c;
+        float* col = Pc + (size_t)c * ld;
+        // pivot: the largest |a_i,kc| over rows i >= kc (ties to the smaller row)
+        float best = (t < n && t >= kc) ? fabsf(col[t]) : -1.0f;
+        int bi = t;
+        for (int off = 16; off > 0; off >>= 1) {
+          const float o = __shfl_down_sync(0xffffffffu, best, off);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
+        }
+        if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
+        __syncthreads();
+        if (warp == 0) {
+          best = lane < NWARP ? wval[lane] : -1.0f;
+          bi = lane < NWARP ? widx[lane] : n;
+          for (int off = 16; off > 0; off >>= 1) {
+            const float o = __shfl_down_sync(0xffffffffu, best, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+            if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
+          }
+          if (lane == 0) {
+            sp = (best > 0.0f) ? bi : kc;
+            if (!(best > 0.0f)) atomicExch(info, 1);
+            ppb[c] = sp;
+          }
+        }
+        __syncthreads();
+        const int p = sp;
+        if (p != kc && t < b) {                 // interchange rows kc and p in the panel's columns
+          float* cc = Pc + (size_t)t * ld;
+          const float tmp = cc[kc];
+          cc[kc] = cc[p];
+          cc[p] = tmp;
+        }
+        __syncthreads();
+        const float pinv = 1.0f / col[kc];
+        if (t < b) r[t] = (t == c ? 1.0f : Pc[(size_t)t * ld + kc]) * pinv;
+        const float fi = (t < n) ? col[t] : 0.0f;
+        __syncthreads();
+        if (t < n) {
+          for (int cc = 0; cc < b; ++cc) {
+            float* a = Pc + (size_t)cc * ld + t;
+            if (t == kc) *a = r[cc];
+            else if (cc == c) *a = -fi * r[c];
+            else *a = fmaf(-fi, r[cc], *a);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    cl.sync();
+    // the panel's pivots and columns, read from the owner through the cluster
+    const int* opp = cl.map_shared_rank(ppb, owner);
+    const float* P = cl.map_shared_rank(A, owner) + (size_t)(k0 - owner * w) * ld;
+    if (t < b) pv[k0 + t] = opp[t];
+    int prow[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) prow[c] = c < b ? opp[c] : 0;
+    const int skip0 = (rank == owner) ? k0 - j0 : nw, skip1 = (rank == owner) ? kend - j0 : nw;
+    for (int jj = t; jj < nw; jj += NT) {
+      if (jj >= skip0 && jj < skip1) continue;
+      float* x = A + (size_t)jj * ld;
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        if (c < b) {
+          const int p = prow[c];
+          if (p != k0 + c) {
+            const float tmp = x[k0 + c];
+            x[k0 + c] = x[p];
+            x[p] = tmp;
+          }
+        }
+      }
+      for (int c = 0; c < b; ++c) {
+        U[(size_t)c * w + jj] = x[k0 + c];
+        x[k0 + c] = 0.0f;
+      }
+    }
+    __syncthreads();
+    if (t < n) {
+      float pr[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) pr[c] = c < b ? P[(size_t)c * ld + t] : 0.0f;
+      for (int jj = 0; jj < nw; ++jj) {
+        if (jj >= skip0 && jj < skip1) continue;
+        float acc = A[(size_t)jj * ld + t];
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc = fmaf(pr[c], U[(size_t)c * w + jj], acc);
+        A[(size_t)jj * ld + t] = acc;
+      }
+    }
+    __syncthreads();
+    k0 = kend;
+  }
+  cl.sync();
+  if (t == 0) {
+    for (int i = 0; i < n; ++i) cur[i] = i;
+    for (int k = n - 1; k >= 0; --k) {
+      const int q = cur[k];
+      cur[k] = cur[pv[k]];
+      cur[pv[k]] = q;
+    }
+    for (int i = 0; i < n; ++i) dest[cur[i]] = i;
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nw; ++jj) {
+    float* out = Ag + (long long)dest[j0 + jj] * n;
+    for (int i = t; i < n; i += NT) out[i] = A[(size_t)jj * ld + i];
+  }
+  if (rank == 0)
+    for (int i = t; i < n; i += NT) piv[e * n + i] = pv[i];
+  cl.sync();
+}
+
 // in-place Gauss-Jordan inversion with partial pivoting of one n x n column-major block per CTA
 // (A[j n + i] = row i, column j). Step k: pick the pivot row in column k, interchange it with row
 // k, scale row k by the reciprocal pivot (the pivot position takes the reciprocal itself) and
@@ -1085,19 +1252,23 @@ static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double 
   return DG_OK;
 }
 
-// the cluster Gauss-Jordan for blocks above one CTA's shared memory: the fewest CTAs (at most 8)
-// whose column slices fit 220 KB each; false (nothing launched) when no cluster fits
+// the blocked cluster Gauss-Jordan for blocks above one CTA's shared memory: the fewest CTAs (at most
+// 8) whose column slices (padded column stride) and panel rows fit 220 KB each; false (nothing
+// launched) when no cluster fits
 static bool gj_cluster(dg_mesh* m, Solver* S, int n, cudaStream_t s) {
-  const long long budget = 220 * 1024 / 4;                      // floats per CTA
-  const long long wmax = (budget - 6LL * n) / (n + 1);
+  constexpr int B = 16;
+  if (n > 640) return false;
+  const long long ld = n | 1;
+  const long long budget = 220 * 1024 / 4 - 3LL * n - 3 * B;    // floats (and ints) per CTA
+  const long long wmax = budget / (ld + B);
   if (wmax < 1) return false;
   const int CL = (int)((n + wmax - 1) / wmax);
   if (CL < 2 || CL > 8) return false;
   const int w = (n + CL - 1) / CL;
-  const size_t smem = sizeof(float) * ((size_t)w * n + 2 * n + w) + sizeof(int) * 3 * (size_t)n;
-  if (n > 640) return false;
-  constexpr int NT = 512;
-  auto kern = (n <= 320) ? k_gj_inverse_cluster<10, NT> : k_gj_inverse_cluster<20, NT>;   // rows per lane
+  const size_t smem = sizeof(float) * ((size_t)w * ld + (size_t)B * w + B) + sizeof(int) * (2 * B + 3 * (size_t)n);
+  const bool big = n > 320;
+  auto kern = big ? k_gj_blocked<640, B> : k_gj_blocked<320, B>;
+  const int NT = big ? 640 : 320;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return false;
