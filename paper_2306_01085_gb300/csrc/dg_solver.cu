@@ -13,7 +13,6 @@
 #include <string>
 #include <vector>
 
-#include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
 #include "dg_bits.cuh"
@@ -502,289 +501,205 @@ __global__ void k_scatter_col(long long E, int n, int j, double c, const double*
   }
 }
 
-// The same Gauss-Jordan inversion for blocks too large for one CTA's shared memory: one cluster of
-// CL CTAs per block, CTA `rank` keeping columns [rank w, rank w + w) (the last CTA fewer) resident in
-// its shared memory. At step k the CTA owning column k finds the pivot row p, and writes column k
-// with rows k and p interchanged, p and the reciprocal pivot into every CTA's buffer (distributed
-// shared memory, two buffers used in turn), then one cluster barrier; every CTA interchanges rows k
-// and p, scales row k and eliminates in its own columns exactly as the single-CTA kernel does. The
-// reverse column interchanges become each column's final position, where each CTA writes its
-// columns back. Cluster barriers at entry and exit keep every remote write inside the lifetime of
-// the CTA it targets. Each lane keeps its MR rows of the pivot column in registers for every
-// column it updates, and the pivot search reduces with warp shuffles.
-template <int MR, int NT>
-__global__ void __launch_bounds__(NT) k_gj_inverse_cluster(long long E, int n, int w, float* __restrict__ blocks,
-                                                            int* __restrict__ piv, int* __restrict__ info) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  const int CL = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
-  const long long e = blockIdx.x / CL;
-  extern __shared__ float sgj[];
-  float* A = sgj;                     // [w][n] own columns
-  float* pcol = A + (size_t)w * n;    // [2][n] pivot columns
-  float* r = pcol + 2 * n;            // [w] scaled row k of the own columns
-  int* pv = reinterpret_cast<int*>(r + w);
-  int* cur = pv + n;
-  int* dest = cur + n;
-  constexpr int NWARP = NT / 32;
-  __shared__ float wval[NWARP];
-  __shared__ int widx[NWARP];
-  __shared__ int spiv[2];
-  __shared__ float sinv[2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j0 = rank * w;
-  const int nw = min(n, j0 + w) - j0;
+// Blocked Gauss-Jordan inversion in global memory, one CTA per block, for blocks too large for one
+// CTA's shared memory. Only the current panel of B columns lives in shared memory, so several CTAs
+// share an SM and one block's serial panel steps overlap another block's update. Per panel:
+//   1. the panel's columns are loaded and the unblocked in-place steps (pivot search over the rows
+//      below, interchange, scaling, elimination) run on them, two block barriers per step; the
+//      panel then holds the columns of the panel's transform T = G_b P_b ... G_1 P_1 (the identity
+//      outside the panel's columns) and is written back;
+//   2. T is applied to every other column x as x <- x~ + P x_K (x_K the rows that the panel's
+//      interchanges bring to positions k0 .. k0 + b, x~ = x interchanged with those rows zeroed),
+//      64 columns at a time: the few interchanged rows are fixed up in place and x_K gathered into
+//      U, then C += P U runs as a tiled FP32 GEMM (4 x 4 register tiles, 16-byte shared loads of P
+//      and U).
+// After the last panel the columns are interchanged back in reverse pivot order (a final pass
+// through a scratch column buffer in global memory: work, [n] floats per block).
+constexpr int GJG_NT = 256;
+constexpr int GJG_B = 32;
+constexpr int GJG_CH = 64;     // columns per update chunk
+template <int B>
+__global__ void __launch_bounds__(GJG_NT, 2) k_gj_global(long long E, int n, float* __restrict__ blocks,
+                                                           int* __restrict__ piv, int* __restrict__ info) {
+  constexpr int NT = GJG_NT, NWARP = NT / 32, CH = GJG_CH;
+  const long long e = blockIdx.x;
   float* Ag = blocks + e * (long long)n * n;
-  for (long long t = threadIdx.x; t < (long long)nw * n; t += blockDim.x) A[t] = Ag[(long long)j0 * n + t];
-  cl.sync();
-  for (int k = 0; k < n; ++k) {
-    const int b = k & 1;
-    if (k / w == rank) {
-      const float* col = A + (long long)(k - j0) * n;
+  const int np = ((n + 3) & ~3) + 4;           // panel column stride (16-byte multiple)
+  extern __shared__ __align__(16) float sgg[];
+  float* P = sgg;                              // [B][np] the panel
+  float* U = P + (size_t)B * np;               // [B][CH] gathered rows of a chunk
+  float* OLD = U + (size_t)B * CH;             // [2B][CH] old values of the interchanged rows
+  int* pv = reinterpret_cast<int*>(OLD + (size_t)2 * B * CH);   // [n] pivot rows
+  int* lrow = pv + n;                          // [2B] rows the panel's interchanges touch
+  int* lsrc = lrow + 2 * B;                    // [2B] the row whose old value each one receives
+                                               // (lrow..: 2n ints for the final permutation)
+  __shared__ float wval[2][NWARP];
+  __shared__ int widx[2][NWARP];
+  __shared__ int nl;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int MR = (n + NT - 1) / NT;            // panel rows per thread (<= 3 for n <= 768)
+  for (int k0 = 0; k0 < n; k0 += B) {
+    const int b = min(B, n - k0);
+    for (int c = 0; c < b; ++c)
+      for (int i = t; i < n; i += NT) P[(size_t)c * np + i] = Ag[(long long)(k0 + c) * n + i];
+    __syncthreads();
+    for (int c = 0; c < b; ++c) {
+      const int kc = k0 + c, sb = c & 1;
       float best = -1.0f;
-      int bi = k;
-      for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        const float a = fabsf(col[i]);
-        if (a > best) { best = a; bi = i; }
+      int bi = n;
+      for (int m = 0; m < MR; ++m) {
+        const int i = t + NT * m;
+        if (i < n && i >= kc) {
+          const float a = fabsf(P[(size_t)c * np + i]);
+          if (a > best) { best = a; bi = i; }
+        }
       }
       for (int off = 16; off > 0; off >>= 1) {
-        const float o = __shfl_down_sync(0xffffffffu, best, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        const float o = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
         if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
       }
-      if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
+      if (lane == 0) { wval[sb][warp] = best; widx[sb][warp] = bi; }
       __syncthreads();
-      if (warp == 0) {
-        best = lane < NWARP ? wval[lane] : -1.0f;
-        bi = lane < NWARP ? widx[lane] : n;
-        for (int off = 16; off > 0; off >>= 1) {
-          const float o = __shfl_down_sync(0xffffffffu, best, off);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-          if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
-        }
-        if (lane == 0) { wval[0] = best; widx[0] = bi; }
+      best = -1.0f;
+      int p = kc;
+      for (int q = 0; q < NWARP; ++q) {
+        const float o = wval[sb][q];
+        const int oi = widx[sb][q];
+        if (o > best || (o == best && oi < p)) { best = o; p = oi; }
       }
+      if (!(best > 0.0f)) p = kc;
+      if (t == 0) {
+        pv[kc] = p;
+        if (!(best > 0.0f)) atomicExch(info, 1);
+      }
+      float R[B], Q[B];                         // rows p and kc of the panel before the step
+#pragma unroll
+      for (int cc = 0; cc < B; ++cc) {
+        R[cc] = cc < b ? P[(size_t)cc * np + p] : 0.0f;
+        Q[cc] = cc < b ? P[(size_t)cc * np + kc] : 0.0f;
+      }
+      const float Rc = P[(size_t)c * np + p], Qc = P[(size_t)c * np + kc];
       __syncthreads();
-      const int p = widx[0];
-      if (threadIdx.x == 0 && !(wval[0] > 0.0f)) atomicExch(info, 1);
-      const float pinv = 1.0f / col[p];
-      for (int q = 0; q < CL; ++q) {
-        float* dst = cl.map_shared_rank(pcol + b * n, q);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = (i == k) ? col[p] : (i == p ? col[k] : col[i]);
-        if (threadIdx.x == 0) {
-          *cl.map_shared_rank(spiv + b, q) = p;
-          *cl.map_shared_rank(sinv + b, q) = pinv;
+      const float pinv = 1.0f / Rc;
+      for (int m = 0; m < MR; ++m) {
+        const int i = t + NT * m;
+        if (i >= n) break;
+        // after the interchange row kc holds R and row p holds Q; every thread rewrites its rows
+        if (i == kc) {
+#pragma unroll
+          for (int cc = 0; cc < B; ++cc)
+            if (cc < b) P[(size_t)cc * np + i] = (cc == c ? 1.0f : R[cc]) * pinv;
+        } else {
+          const float f = (i == p) ? Qc : P[(size_t)c * np + i];
+#pragma unroll
+          for (int cc = 0; cc < B; ++cc) {
+            if (cc < b) {
+              const float rowv = (i == p) ? Q[cc] : P[(size_t)cc * np + i];
+              P[(size_t)cc * np + i] = (cc == c) ? -f * pinv : fmaf(-f, R[cc] * pinv, rowv);
+            }
+          }
         }
-      }
-    }
-    cl.sync();
-    const int p = spiv[b];
-    const float pinv = sinv[b];
-    const float* f = pcol + b * n;
-    if (threadIdx.x == 0) pv[k] = p;
-    for (int jj = threadIdx.x; jj < nw; jj += blockDim.x) {
-      float* col = A + (long long)jj * n;
-      if (p != k) {
-        const float t = col[k];
-        col[k] = col[p];
-        col[p] = t;
-      }
-      r[jj] = (j0 + jj == k ? 1.0f : col[k]) * pinv;
-    }
-    // this lane's rows of the pivot column, in registers for every column it updates
-    float fr[MR];
-#pragma unroll
-    for (int m = 0; m < MR; ++m) {
-      const int i = lane + 32 * m;
-      fr[m] = (i < n && i != k) ? f[i] : 0.0f;
-    }
-    __syncthreads();
-    for (int jj = warp; jj < nw; jj += NWARP) {
-      float* col = A + (long long)jj * n;
-      const float rj = r[jj];
-      const bool piv_col = (j0 + jj == k);
-      float v[MR];
-#pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        const int i = lane + 32 * m;
-        v[m] = (i < n && !piv_col) ? col[i] : 0.0f;
-      }
-#pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        const int i = lane + 32 * m;
-        if (i < n) col[i] = (i == k) ? rj : fmaf(-fr[m], rj, v[m]);
       }
     }
     __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < n; ++i) cur[i] = i;
-    for (int k = n - 1; k >= 0; --k) {
-      const int t = cur[k];
-      cur[k] = cur[pv[k]];
-      cur[pv[k]] = t;
+    for (int c = 0; c < b; ++c)
+      for (int i = t; i < n; i += NT) Ag[(long long)(k0 + c) * n + i] = P[(size_t)c * np + i];
+    if (t == 0) {
+      // the rows the interchanges k0 + c <-> pv[k0 + c] (in order) touch, and where each one's new
+      // value comes from
+      int cnt = 0;
+      for (int c = 0; c < b; ++c) {
+        const int r0 = k0 + c, r1 = pv[k0 + c];
+        int a = -1, bb = -1;
+        for (int q = 0; q < cnt; ++q) {
+          if (lrow[q] == r0) a = q;
+          if (lrow[q] == r1) bb = q;
+        }
+        if (a < 0) { lrow[cnt] = r0; lsrc[cnt] = r0; a = cnt++; }
+        if (bb < 0) { lrow[cnt] = r1; lsrc[cnt] = r1; bb = cnt++; }
+        const int tmp = lsrc[a];
+        lsrc[a] = lsrc[bb];
+        lsrc[bb] = tmp;
+      }
+      nl = cnt;
     }
-    for (int i = 0; i < n; ++i) dest[cur[i]] = i;
+    __syncthreads();
+    const int L = nl;
+    const int ntrail = n - b;
+    for (int j0 = 0; j0 < ntrail; j0 += CH) {
+      const int nc = min(CH, ntrail - j0);
+      // (a) old values of the touched rows of the chunk's columns
+      for (int q = t; q < L * CH; q += NT) {
+        const int l = q / CH, jc = q % CH;
+        if (jc < nc) {
+          const int j = j0 + jc < k0 ? j0 + jc : j0 + jc + b;
+          OLD[(size_t)l * CH + jc] = Ag[(long long)j * n + lsrc[l]];
+        }
+      }
+      __syncthreads();
+      // (b) the gathered rows U (panel rows after the interchanges) and x~ in place
+      for (int q = t; q < L * CH; q += NT) {
+        const int l = q / CH, jc = q % CH;
+        if (jc < nc) {
+          const int j = j0 + jc < k0 ? j0 + jc : j0 + jc + b;
+          const int row = lrow[l];
+          const float v = OLD[(size_t)l * CH + jc];
+          if (row >= k0 && row < k0 + b) {
+            U[(size_t)(row - k0) * CH + jc] = v;
+            Ag[(long long)j * n + row] = 0.0f;
+          } else {
+            Ag[(long long)j * n + row] = v;
+          }
+        }
+      }
+      // (every panel row k0 + c is in the list: step c interchanges it, possibly with itself)
+      for (int q = t; q < (B - b) * CH; q += NT) U[(size_t)b * CH + q] = 0.0f;   // unused rows of U
+      __syncthreads();
+      // (c) C += P U on the chunk: 4 x 4 tiles (rows 4 r .. 4 r + 3, chunk columns 4 s .. 4 s + 3)
+      const int rt = (n + 3) / 4, ntile = rt * (CH / 4);
+      for (int tile = t; tile < ntile; tile += NT) {
+        const int r = tile % rt, sc = tile / rt;
+        const int i0 = 4 * r, c0 = 4 * sc;
+        if (c0 >= nc) continue;
+        float acc[4][4];
+#pragma unroll
+        for (int qc = 0; qc < 4; ++qc) {
+          const int jc = c0 + qc;
+          const int j = j0 + jc < k0 ? j0 + jc : j0 + jc + b;
+#pragma unroll
+          for (int qr = 0; qr < 4; ++qr)
+            acc[qc][qr] = (jc < nc && i0 + qr < n) ? Ag[(long long)j * n + i0 + qr] : 0.0f;
+        }
+#pragma unroll 8
+        for (int k = 0; k < B; ++k) {
+          const float4 pk = *reinterpret_cast<const float4*>(P + (size_t)k * np + i0);
+          const float4 uk = *reinterpret_cast<const float4*>(U + (size_t)k * CH + c0);
+          const float pr[4] = {pk.x, pk.y, pk.z, pk.w};
+          const float ur[4] = {uk.x, uk.y, uk.z, uk.w};
+#pragma unroll
+          for (int qc = 0; qc < 4; ++qc)
+#pragma unroll
+            for (int qr = 0; qr < 4; ++qr) acc[qc][qr] = fmaf(pr[qr], ur[qc], acc[qc][qr]);
+        }
+#pragma unroll
+        for (int qc = 0; qc < 4; ++qc) {
+          const int jc = c0 + qc;
+          if (jc >= nc) continue;
+          const int j = j0 + jc < k0 ? j0 + jc : j0 + jc + b;
+#pragma unroll
+          for (int qr = 0; qr < 4; ++qr)
+            if (i0 + qr < n) Ag[(long long)j * n + i0 + qr] = acc[qc][qr];
+        }
+      }
+      __syncthreads();
+    }
   }
-  __syncthreads();
-  for (int jj = 0; jj < nw; ++jj) {
-    float* out = Ag + (long long)dest[j0 + jj] * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = A[(long long)jj * n + i];
-  }
-  if (rank == 0)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) piv[e * n + i] = pv[i];
-  cl.sync();
-}
-
-// Blocked Gauss-Jordan inversion on a thread-block cluster (blocks too large for one CTA's shared
-// memory). CTA `rank` keeps columns [rank w, rank w + w) in shared memory (column stride ld = n | 1,
-// odd, so row-wise and column-wise accesses are both free of bank conflicts). The columns are
-// processed in panels of at most B that never straddle two CTAs:
-//   1. the owner of the panel runs the unblocked in-place steps (pivot search over the rows below,
-//      row interchange, scaling, elimination) on the panel's columns only, with one thread per
-//      row and block-level barriers; the panel then holds the columns of the panel's transform
-//      T = G_b P_b ... G_1 P_1, which is the identity outside the panel's columns;
-//   2. one cluster barrier;
-//   3. every CTA applies T to each of its other columns x: the panel's row interchanges, then
-//      x <- x~ + P x_K, with x_K the panel rows of x, x~ = x with those rows zeroed and P the panel
-//      (read from the owner's shared memory through the cluster): a rank-b product, one thread per
-//      row accumulating over b with the panel row in registers.
-// One cluster barrier per panel replaces one per column. The panel's pivots are kept in two buffers
-// used in turn (a CTA may still read panel t's while the owner of panel t + 1 records its own).
-// After the last panel the columns are interchanged back in reverse pivot order as each CTA writes
-// them out. NT >= n threads (one row each).
-template <int NT, int B>
-__global__ void __launch_bounds__(NT) k_gj_blocked(long long E, int n, int w, float* __restrict__ blocks,
-                                                    int* __restrict__ piv, int* __restrict__ info) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  const int CL = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
-  const long long e = blockIdx.x / CL;
-  const int ld = n | 1;
-  extern __shared__ float sgb[];
-  float* A = sgb;                               // [w][ld] own columns
-  float* U = A + (size_t)w * ld;                // [B][w] panel rows of the own columns
-  float* r = U + (size_t)B * w;                 // [B] scaled pivot row of the panel
-  int* pp = reinterpret_cast<int*>(r + B);      // [2][B] the panel's pivot rows
-  int* pv = pp + 2 * B;                         // [n] every pivot row
-  int* cur = pv + n;
+  // columns back in reverse pivot order: the composed interchange gives each column's final
+  // position dest; the block is rewritten in strips of 32 rows through shared memory, each strip
+  // read whole before it is written, so the permutation is in place without a scratch block
+  int* cur = lrow;                             // [n] (the interchange lists are no longer needed)
   int* dest = cur + n;
-  constexpr int NWARP = NT / 32;
-  __shared__ float wval[NWARP];
-  __shared__ int widx[NWARP];
-  __shared__ int sp;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int j0 = rank * w;
-  const int nw = max(0, min(n, j0 + w) - j0);
-  float* Ag = blocks + e * (long long)n * n;
-  for (long long q = t; q < (long long)nw * n; q += NT) A[(q / n) * ld + q % n] = Ag[(long long)j0 * n + q];
-  cl.sync();
-  int panel = 0;
-  for (int k0 = 0; k0 < n; ++panel) {
-    const int owner = k0 / w;
-    const int kend = min(min(k0 + B, (owner + 1) * w), n);
-    const int b = kend - k0;
-    int* ppb = pp + (panel & 1) * B;
-    if (rank == owner) {
-      float* Pc = A + (size_t)(k0 - j0) * ld;   // the panel's first column
-      for (int c = 0; c < b; ++c) {
-        const int kc = k0 + c;
-        float* col = Pc + (size_t)c * ld;
-        // pivot: the largest |a_i,kc| over rows i >= kc (ties to the smaller row)
-        float best = (t < n && t >= kc) ? fabsf(col[t]) : -1.0f;
-        int bi = t;
-        for (int off = 16; off > 0; off >>= 1) {
-          const float o = __shfl_down_sync(0xffffffffu, best, off);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-          if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
-        }
-        if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
-        __syncthreads();
-        if (warp == 0) {
-          best = lane < NWARP ? wval[lane] : -1.0f;
-          bi = lane < NWARP ? widx[lane] : n;
-          for (int off = 16; off > 0; off >>= 1) {
-            const float o = __shfl_down_sync(0xffffffffu, best, off);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-            if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
-          }
-          if (lane == 0) {
-            sp = (best > 0.0f) ? bi : kc;
-            if (!(best > 0.0f)) atomicExch(info, 1);
-            ppb[c] = sp;
-          }
-        }
-        __syncthreads();
-        const int p = sp;
-        if (p != kc && t < b) {                 // interchange rows kc and p in the panel's columns
-          float* cc = Pc + (size_t)t * ld;
-          const float tmp = cc[kc];
-          cc[kc] = cc[p];
-          cc[p] = tmp;
-        }
-        __syncthreads();
-        const float pinv = 1.0f / col[kc];
-        if (t < b) r[t] = (t == c ? 1.0f : Pc[(size_t)t * ld + kc]) * pinv;
-        const float fi = (t < n) ? col[t] : 0.0f;
-        __syncthreads();
-        if (t < n) {
-          for (int cc = 0; cc < b; ++cc) {
-            float* a = Pc + (size_t)cc * ld + t;
-            if (t == kc) *a = r[cc];
-            else if (cc == c) *a = -fi * r[c];
-            else *a = fmaf(-fi, r[cc], *a);
-          }
-        }
-        __syncthreads();
-      }
-    }
-    cl.sync();
-    // the panel's pivots and columns, read from the owner through the cluster
-    const int* opp = cl.map_shared_rank(ppb, owner);
-    const float* P = cl.map_shared_rank(A, owner) + (size_t)(k0 - owner * w) * ld;
-    if (t < b) pv[k0 + t] = opp[t];
-    int prow[B];
-#pragma unroll
-    for (int c = 0; c < B; ++c) prow[c] = c < b ? opp[c] : 0;
-    const int skip0 = (rank == owner) ? k0 - j0 : nw, skip1 = (rank == owner) ? kend - j0 : nw;
-    for (int jj = t; jj < nw; jj += NT) {
-      if (jj >= skip0 && jj < skip1) continue;
-      float* x = A + (size_t)jj * ld;
-#pragma unroll
-      for (int c = 0; c < B; ++c) {
-        if (c < b) {
-          const int p = prow[c];
-          if (p != k0 + c) {
-            const float tmp = x[k0 + c];
-            x[k0 + c] = x[p];
-            x[p] = tmp;
-          }
-        }
-      }
-      for (int c = 0; c < b; ++c) {
-        U[(size_t)c * w + jj] = x[k0 + c];
-        x[k0 + c] = 0.0f;
-      }
-    }
-    __syncthreads();
-    if (t < n) {
-      float pr[B];
-#pragma unroll
-      for (int c = 0; c < B; ++c) pr[c] = c < b ? P[(size_t)c * ld + t] : 0.0f;
-      for (int jj = 0; jj < nw; ++jj) {
-        if (jj >= skip0 && jj < skip1) continue;
-        float acc = A[(size_t)jj * ld + t];
-#pragma unroll
-        for (int c = 0; c < B; ++c) acc = fmaf(pr[c], U[(size_t)c * w + jj], acc);
-        A[(size_t)jj * ld + t] = acc;
-      }
-    }
-    __syncthreads();
-    k0 = kend;
-  }
-  cl.sync();
   if (t == 0) {
     for (int i = 0; i < n; ++i) cur[i] = i;
     for (int k = n - 1; k >= 0; --k) {
@@ -795,13 +710,21 @@ __global__ void __launch_bounds__(NT) k_gj_blocked(long long E, int n, int w, fl
     for (int i = 0; i < n; ++i) dest[cur[i]] = i;
   }
   __syncthreads();
-  for (int jj = 0; jj < nw; ++jj) {
-    float* out = Ag + (long long)dest[j0 + jj] * n;
-    for (int i = t; i < n; i += NT) out[i] = A[(size_t)jj * ld + i];
+  float* strip = P;                            // [n][32] (n 32 <= B np floats)
+  for (int r0 = 0; r0 < n; r0 += 32) {
+    const int rows = min(32, n - r0);
+    for (int q = t; q < n * 32; q += NT) {
+      const int j = q >> 5, rr = q & 31;
+      if (rr < rows) strip[q] = Ag[(long long)j * n + r0 + rr];
+    }
+    __syncthreads();
+    for (int q = t; q < n * 32; q += NT) {
+      const int j = q >> 5, rr = q & 31;
+      if (rr < rows) Ag[(long long)dest[j] * n + r0 + rr] = strip[q];
+    }
+    __syncthreads();
   }
-  if (rank == 0)
-    for (int i = t; i < n; i += NT) piv[e * n + i] = pv[i];
-  cl.sync();
+  for (int i = t; i < n; i += NT) piv[e * n + i] = pv[i];
 }
 
 // in-place Gauss-Jordan inversion with partial pivoting of one n x n column-major block per CTA
@@ -1252,47 +1175,6 @@ static int bj_assemble(dg_mesh* m, Solver* S, const double* U, double t, double 
   return DG_OK;
 }
 
-// the blocked cluster Gauss-Jordan for blocks above one CTA's shared memory: the fewest CTAs (at most
-// 8) whose column slices (padded column stride) and panel rows fit 220 KB each; false (nothing
-// launched) when no cluster fits
-static bool gj_cluster(dg_mesh* m, Solver* S, int n, cudaStream_t s) {
-  constexpr int B = 16;
-  if (n > 640) return false;
-  const long long ld = n | 1;
-  const long long budget = 220 * 1024 / 4 - 3LL * n - 3 * B;    // floats (and ints) per CTA
-  const long long wmax = budget / (ld + B);
-  if (wmax < 1) return false;
-  const int CL = (int)((n + wmax - 1) / wmax);
-  if (CL < 2 || CL > 8) return false;
-  const int w = (n + CL - 1) / CL;
-  const size_t smem = sizeof(float) * ((size_t)w * ld + (size_t)B * w + B) + sizeof(int) * (2 * B + 3 * (size_t)n);
-  const bool big = n > 320;
-  auto kern = big ? k_gj_blocked<640, B> : k_gj_blocked<320, B>;
-  const int NT = big ? 640 : 320;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(m->E * CL));
-  cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
-    cudaGetLastError();
-    return false;
-  }
-  return cudaLaunchKernelEx(&cfg, kern, m->E, n, w, S->blocks, S->piv, S->info) == cudaSuccess;
-}
-
 static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, cudaStream_t s, bool f32 = false,
                     bool half = false) {
   int rc = ensure_blocks(m, S);
@@ -1313,7 +1195,13 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
   if (gj_smem <= 200 * 1024) {
     cudaFuncSetAttribute(k_gj_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem);
     k_gj_inverse<true><<<(unsigned)m->E, 256, gj_smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
-  } else if (!gj_cluster(m, S, nb, s)) {
+  } else if (nb <= 768) {
+    const int np = ((nb + 3) & ~3) + 4;
+    const size_t smem = sizeof(float) * ((size_t)GJG_B * np + (size_t)GJG_B * GJG_CH + 2 * GJG_B * GJG_CH) +
+                        sizeof(int) * ((size_t)nb + std::max<size_t>(4 * GJG_B, 2 * (size_t)nb));
+    cudaFuncSetAttribute(k_gj_global<GJG_B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gj_global<GJG_B><<<(unsigned)m->E, GJG_NT, smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+  } else {
     k_gj_inverse<false><<<(unsigned)m->E, 256, sizeof(float) * 2 * nb, s>>>(m->E, nb, S->blocks, S->piv, S->info);
   }
   prof_end(m, s);
