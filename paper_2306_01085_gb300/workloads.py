@@ -234,6 +234,9 @@ CONFIGS = {
                           "cubed-sphere shell 6x48x48x16, p=3, EUV"),
     "shell24x8_p3_euv": (lambda: shell_desc(n=24, nr=8, p=3, euv=True),
                          "cubed-sphere shell 6x24x24x8, p=3, EUV (small profiling case, 8.8M DOF)"),
+    "shell8x4_p3_euv": (lambda: shell_desc(n=8, nr=4, p=3, euv=True),
+                        "cubed-sphere shell 6x8x8x4, p=3, EUV (profiling case for the 320^2 block inversion, "
+                        "1,536 blocks)"),
 }
 
 

@@ -11,6 +11,7 @@ from paper_2306_01085_gb300 import workloads as W
     ("shell16x8_p4", 12_288, 4, 7_680_000),
     ("shell24x8_p2_euv", 27_648, 2, 3_732_480),
     ("shell24x8_p3_euv", 27_648, 3, 8_847_360),
+    ("shell8x4_p3_euv", 1_536, 3, 491_520),
     ("shell32x16_p2_euv", 98_304, 2, 13_271_040),
     ("shell32x16_p2_euvac", 98_304, 2, 13_271_040),
     ("shell32x16_p2_comp", 98_304, 2, 13_271_040),
