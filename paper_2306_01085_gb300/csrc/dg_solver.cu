@@ -502,166 +502,312 @@ __global__ void k_scatter_col(long long E, int n, int j, double c, const double*
 }
 
 // Blocked Gauss-Jordan inversion in global memory, one CTA per block, for blocks too large for one
-// CTA's shared memory. Only the current panel of B columns lives in shared memory, so several CTAs
-// share an SM and one block's serial panel steps overlap another block's update. Per panel:
-//   1. the panel's columns are loaded and the unblocked in-place steps (pivot search over the rows
-//      below, interchange, scaling, elimination) run on them, two block barriers per step; the
-//      panel then holds the columns of the panel's transform T = G_b P_b ... G_1 P_1 (the identity
-//      outside the panel's columns) and is written back;
-//   2. T is applied to every other column x as x <- x~ + P x_K (x_K the rows that the panel's
-//      interchanges bring to positions k0 .. k0 + b, x~ = x interchanged with those rows zeroed),
-//      64 columns at a time: the few interchanged rows are fixed up in place and x_K gathered into
-//      U, then C += P U runs as a tiled FP32 GEMM (4 x 4 register tiles, 16-byte shared loads of P
-//      and U).
-// After the last panel the columns are interchanged back in reverse pivot order (a final pass
-// through a scratch column buffer in global memory: work, [n] floats per block).
-constexpr int GJG_NT = 256;
+// CTA's shared memory. Only the current panel of B columns is staged, so two CTAs share an SM and one
+// block's serial panel steps overlap another block's update. Row interchanges are not applied to
+// the matrix: a permutation pi (logical row -> row in memory) records them, so a panel's pivoting
+// costs no traffic in the other columns. Per panel:
+//   1. the panel's rows are gathered through pi into registers (rows t, t + NT, t + 2 NT of thread
+//      t) and the unblocked in-place steps run there: each step needs one block barrier, before
+//      which the lane holding each warp's pivot candidate and the holder of row k publish their
+//      rows in small double-buffered slots; after it every thread picks the pivot p, swaps pi[k]
+//      and pi[p] (thread 0), and rewrites its own rows (rows k and p take the interchanged and
+//      scaled values). The panel then holds the columns of the panel's transform
+//      T = G_b P_b ... G_1 P_1, the identity outside the panel's columns, and is scattered back
+//      through pi into the block and into shared memory in memory-row order;
+//   2. T acts on every other column x as x <- x~ + P x_K (x_K the logical rows k0 .. k0 + b, x~ = x
+//      with those rows zeroed): 64 columns at a time, x_K is gathered through pi into U and
+//      C += P U runs as a tiled FP32 GEMM in memory-row order (4 x 4 register tiles, 16-byte shared
+//      loads of P and U), the rows of x_K reading as zero.
+// At the end every column is un-permuted through pi, and the columns are interchanged back in
+// reverse pivot order, in strips of 32 rows read whole before they are written.
 constexpr int GJG_B = 32;
 constexpr int GJG_CH = 64;     // columns per update chunk
-template <int B>
-__global__ void __launch_bounds__(GJG_NT, 2) k_gj_global(long long E, int n, float* __restrict__ blocks,
-                                                           int* __restrict__ piv, int* __restrict__ info) {
-  constexpr int NT = GJG_NT, NWARP = NT / 32, CH = GJG_CH;
+
+// The B steps of a full panel with the step index known at compile time: every row then needs one
+// FMA per entry. Each warp's candidate lane publishes its row already scaled by the reciprocal of its
+// pivot-column entry (r_j = x_j / x_c, r_c = 1 / x_c), the holder of row k publishes row k as it is;
+// after the barrier, rows other than k and p take x_j - x_c r_j (x_c -> -x_c r_c), row k takes r and
+// row p (the old row k) takes q_j - q_c r_j.
+template <int B, int MRT, int NT>
+__device__ __forceinline__ void gj_panel_full(float (&rv)[MRT][B], int n, int k0, float* __restrict__ slot,
+                                              float (*wval)[NT / 32], int (*widx)[NT / 32], int* __restrict__ pv,
+                                              int* __restrict__ pi, int* __restrict__ info) {
+  constexpr int NWARP = NT / 32;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const int kc = k0 + c, sb = c & 1;
+    float best = -1.0f;
+    int bi = n, bm = 0;
+#pragma unroll
+    for (int m = 0; m < MRT; ++m) {
+      const int i = t + NT * m;
+      if (i < n && i >= kc) {
+        const float a = fabsf(rv[m][c]);
+        if (a > best) { best = a; bi = i; bm = m; }
+      }
+    }
+    float wb = best;
+    int wi = bi;
+    for (int off = 16; off > 0; off >>= 1) {
+      const float o = __shfl_xor_sync(0xffffffffu, wb, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, wi, off);
+      if (o > wb || (o == wb && oi < wi)) { wb = o; wi = oi; }
+    }
+    float* ws = slot + ((size_t)sb * (NWARP + 1) + warp) * B;
+    float* ks = slot + ((size_t)sb * (NWARP + 1) + NWARP) * B;
+    if (wi == bi && wi < n) {
+#pragma unroll
+      for (int m = 0; m < MRT; ++m)
+        if (m == bm) {
+          const float rinv = 1.0f / rv[m][c];
+#pragma unroll
+          for (int q = 0; q < B / 4; ++q) {
+            float4 v;
+            v.x = (4 * q + 0 == c) ? rinv : rv[m][4 * q + 0] * rinv;
+            v.y = (4 * q + 1 == c) ? rinv : rv[m][4 * q + 1] * rinv;
+            v.z = (4 * q + 2 == c) ? rinv : rv[m][4 * q + 2] * rinv;
+            v.w = (4 * q + 3 == c) ? rinv : rv[m][4 * q + 3] * rinv;
+            *reinterpret_cast<float4*>(ws + 4 * q) = v;
+          }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < MRT; ++m)
+      if (t + NT * m == kc)
+#pragma unroll
+        for (int q = 0; q < B / 4; ++q)
+          *reinterpret_cast<float4*>(ks + 4 * q) =
+              make_float4(rv[m][4 * q], rv[m][4 * q + 1], rv[m][4 * q + 2], rv[m][4 * q + 3]);
+    if (lane == 0) { wval[sb][warp] = wb; widx[sb][warp] = wi; }
+    __syncthreads();
+    float pb = -1.0f;
+    int p = kc, wq = 0;
+    for (int q = 0; q < NWARP; ++q) {
+      const float o = wval[sb][q];
+      const int oi = widx[sb][q];
+      if (o > pb || (o == pb && oi < p)) { pb = o; p = oi; wq = q; }
+    }
+    const bool ok = pb > 0.0f;
+    if (!ok) p = kc;
+    const float* r = slot + ((size_t)sb * (NWARP + 1) + wq) * B;   // the scaled pivot row
+    if (t == 0) {
+      pv[kc] = p;
+      if (!ok) atomicExch(info, 1);
+      const int a = pi[kc];
+      pi[kc] = pi[p];
+      pi[p] = a;
+    }
+#pragma unroll
+    for (int q = 0; q < B / 4; ++q) {
+      const float4 r4 = *reinterpret_cast<const float4*>(r + 4 * q);
+      const float rq[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+      for (int m = 0; m < MRT; ++m) {
+        if (MRT > 1 && m > 0 && (t - lane) + NT * m >= n) continue;   // warp-uniform: no rows here
+        const float f = rv[m][c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cc = 4 * q + u;
+          if (cc == c) continue;
+          rv[m][cc] = fmaf(-f, rq[u], rv[m][cc]);
+        }
+      }
+    }
+    const float rc = r[c];
+#pragma unroll
+    for (int m = 0; m < MRT; ++m) {
+      const int i = t + NT * m;
+      if (i == kc) {
+#pragma unroll
+        for (int cc = 0; cc < B; ++cc) rv[m][cc] = r[cc];
+      } else if (i == p) {
+        const float fq = ks[c];
+#pragma unroll
+        for (int cc = 0; cc < B; ++cc) rv[m][cc] = (cc == c) ? -fq * rc : fmaf(-fq, r[cc], ks[cc]);
+      } else {
+        rv[m][c] = -rv[m][c] * rc;
+      }
+    }
+  }
+}
+
+template <int B, int MRT, int NT>
+__global__ void __launch_bounds__(NT, 2) k_gj_global(long long E, int n, float* __restrict__ blocks,
+                                                     int* __restrict__ piv, int* __restrict__ info) {
+  constexpr int NWARP = NT / 32, CH = GJG_CH;
   const long long e = blockIdx.x;
   float* Ag = blocks + e * (long long)n * n;
   const int np = ((n + 3) & ~3) + 4;           // panel column stride (16-byte multiple)
   extern __shared__ __align__(16) float sgg[];
-  float* P = sgg;                              // [B][np] the panel
+  float* P = sgg;                              // [B][np] the panel, memory-row order
   float* U = P + (size_t)B * np;               // [B][CH] gathered rows of a chunk
-  float* OLD = U + (size_t)B * CH;             // [2B][CH] old values of the interchanged rows
-  int* pv = reinterpret_cast<int*>(OLD + (size_t)2 * B * CH);   // [n] pivot rows
-  int* lrow = pv + n;                          // [2B] rows the panel's interchanges touch
-  int* lsrc = lrow + 2 * B;                    // [2B] the row whose old value each one receives
-                                               // (lrow..: 2n ints for the final permutation)
+  float* slot = U + (size_t)B * CH;            // [2][NWARP + 1][B] candidate rows and row k
+  int* pv = reinterpret_cast<int*>(slot + 2 * (NWARP + 1) * B);   // [n] pivot rows
+  int* pi = pv + n;                            // [n] logical row -> memory row
+  int* mask = pi + n;                          // [n] memory rows of the current panel's rows
+  int* dest = mask + n;                        // [n] final column positions
   __shared__ float wval[2][NWARP];
   __shared__ int widx[2][NWARP];
-  __shared__ int nl;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int MR = (n + NT - 1) / NT;            // panel rows per thread (<= 3 for n <= 768)
+  for (int i = t; i < n; i += NT) {
+    pi[i] = i;
+    mask[i] = 0;
+  }
+  __syncthreads();
   for (int k0 = 0; k0 < n; k0 += B) {
     const int b = min(B, n - k0);
-    for (int c = 0; c < b; ++c)
-      for (int i = t; i < n; i += NT) P[(size_t)c * np + i] = Ag[(long long)(k0 + c) * n + i];
-    __syncthreads();
+    // 1. the panel's rows in registers
+    float rv[MRT][B];
+#pragma unroll
+    for (int m = 0; m < MRT; ++m) {
+      const int i = t + NT * m;
+      const int src = i < n ? pi[i] : 0;
+#pragma unroll
+      for (int c = 0; c < B; ++c) rv[m][c] = (i < n && c < b) ? Ag[(long long)(k0 + c) * n + src] : 0.0f;
+    }
+    if (MRT == 1 && b == B) {
+      gj_panel_full<B, MRT, NT>(rv, n, k0, slot, wval, widx, pv, pi, info);
+    } else {
+    float cv[MRT];                             // each own row's entry in the current pivot column
+#pragma unroll
+    for (int m = 0; m < MRT; ++m) cv[m] = rv[m][0];
     for (int c = 0; c < b; ++c) {
       const int kc = k0 + c, sb = c & 1;
       float best = -1.0f;
-      int bi = n;
-      for (int m = 0; m < MR; ++m) {
+      int bi = n, bm = 0;
+#pragma unroll
+      for (int m = 0; m < MRT; ++m) {
         const int i = t + NT * m;
         if (i < n && i >= kc) {
-          const float a = fabsf(P[(size_t)c * np + i]);
-          if (a > best) { best = a; bi = i; }
+          const float a = fabsf(cv[m]);
+          if (a > best) { best = a; bi = i; bm = m; }
         }
       }
+      float wb = best;
+      int wi = bi;
       for (int off = 16; off > 0; off >>= 1) {
-        const float o = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (o > best || (o == best && oi < bi)) { best = o; bi = oi; }
+        const float o = __shfl_xor_sync(0xffffffffu, wb, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, wi, off);
+        if (o > wb || (o == wb && oi < wi)) { wb = o; wi = oi; }
       }
-      if (lane == 0) { wval[sb][warp] = best; widx[sb][warp] = bi; }
+      float* ws = slot + ((size_t)sb * (NWARP + 1) + warp) * B;
+      float* ks = slot + ((size_t)sb * (NWARP + 1) + NWARP) * B;
+      if (wi == bi && wi < n) {                // this lane holds the warp's candidate row
+#pragma unroll
+        for (int m = 0; m < MRT; ++m)
+          if (m == bm)
+#pragma unroll
+            for (int cc = 0; cc < B; ++cc) ws[cc] = rv[m][cc];
+      }
+#pragma unroll
+      for (int m = 0; m < MRT; ++m)
+        if (t + NT * m == kc)
+#pragma unroll
+          for (int cc = 0; cc < B; ++cc) ks[cc] = rv[m][cc];
+      if (lane == 0) { wval[sb][warp] = wb; widx[sb][warp] = wi; }
       __syncthreads();
       best = -1.0f;
-      int p = kc;
+      int p = kc, wq = 0;
       for (int q = 0; q < NWARP; ++q) {
         const float o = wval[sb][q];
         const int oi = widx[sb][q];
-        if (o > best || (o == best && oi < p)) { best = o; p = oi; }
+        if (o > best || (o == best && oi < p)) { best = o; p = oi; wq = q; }
       }
-      if (!(best > 0.0f)) p = kc;
+      const bool ok = best > 0.0f;
+      if (!ok) p = kc;
+      const float* R = ok ? slot + ((size_t)sb * (NWARP + 1) + wq) * B : ks;   // old row p
       if (t == 0) {
         pv[kc] = p;
-        if (!(best > 0.0f)) atomicExch(info, 1);
+        if (!ok) atomicExch(info, 1);
+        const int a = pi[kc];
+        pi[kc] = pi[p];
+        pi[p] = a;
       }
-      float R[B], Q[B];                         // rows p and kc of the panel before the step
+      const float pinv = 1.0f / R[c];
+      float cvn[MRT];
+#pragma unroll
+      for (int m = 0; m < MRT; ++m) cvn[m] = 0.0f;
+      // every row: x <- x - x_c r with r = R / R_c, and x_c <- -x_c / R_c in the pivot column
 #pragma unroll
       for (int cc = 0; cc < B; ++cc) {
-        R[cc] = cc < b ? P[(size_t)cc * np + p] : 0.0f;
-        Q[cc] = cc < b ? P[(size_t)cc * np + kc] : 0.0f;
+        if (cc < b) {
+          const float r = R[cc] * pinv;
+#pragma unroll
+          for (int m = 0; m < MRT; ++m) {
+            const float v = (cc == c) ? -cv[m] * pinv : fmaf(-cv[m], r, rv[m][cc]);
+            rv[m][cc] = v;
+            if (cc == c + 1) cvn[m] = v;
+          }
+        }
       }
-      const float Rc = P[(size_t)c * np + p], Qc = P[(size_t)c * np + kc];
-      __syncthreads();
-      const float pinv = 1.0f / Rc;
-      for (int m = 0; m < MR; ++m) {
+      // rows k and p after the interchange: row k is R scaled, row p is the old row k eliminated
+#pragma unroll
+      for (int m = 0; m < MRT; ++m) {
         const int i = t + NT * m;
-        if (i >= n) break;
-        // after the interchange row kc holds R and row p holds Q; every thread rewrites its rows
         if (i == kc) {
 #pragma unroll
-          for (int cc = 0; cc < B; ++cc)
-            if (cc < b) P[(size_t)cc * np + i] = (cc == c ? 1.0f : R[cc]) * pinv;
-        } else {
-          const float f = (i == p) ? Qc : P[(size_t)c * np + i];
+          for (int cc = 0; cc < B; ++cc) {
+            const float v = (cc == c) ? pinv : R[cc] * pinv;
+            rv[m][cc] = v;
+            if (cc == c + 1) cvn[m] = v;
+          }
+        } else if (i == p) {
+          const float f = ks[c];
 #pragma unroll
           for (int cc = 0; cc < B; ++cc) {
-            if (cc < b) {
-              const float rowv = (i == p) ? Q[cc] : P[(size_t)cc * np + i];
-              P[(size_t)cc * np + i] = (cc == c) ? -f * pinv : fmaf(-f, R[cc] * pinv, rowv);
-            }
+            const float v = (cc == c) ? -f * pinv : fmaf(-f, R[cc] * pinv, ks[cc]);
+            rv[m][cc] = v;
+            if (cc == c + 1) cvn[m] = v;
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < MRT; ++m) cv[m] = cvn[m];
+    }
+    }
+    __syncthreads();                           // pi holds this panel's interchanges
+    // the panel back into the block and into shared memory, at the rows' memory positions
+#pragma unroll
+    for (int m = 0; m < MRT; ++m) {
+      const int i = t + NT * m;
+      if (i < n) {
+        const int dst = pi[i];
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          if (c < b) {
+            Ag[(long long)(k0 + c) * n + dst] = rv[m][c];
+            P[(size_t)c * np + dst] = rv[m][c];
+          } else {
+            P[(size_t)c * np + dst] = 0.0f;
           }
         }
       }
     }
+    for (int c = t; c < b; c += NT) mask[pi[k0 + c]] = 1;
     __syncthreads();
-    for (int c = 0; c < b; ++c)
-      for (int i = t; i < n; i += NT) Ag[(long long)(k0 + c) * n + i] = P[(size_t)c * np + i];
-    if (t == 0) {
-      // the rows the interchanges k0 + c <-> pv[k0 + c] (in order) touch, and where each one's new
-      // value comes from
-      int cnt = 0;
-      for (int c = 0; c < b; ++c) {
-        const int r0 = k0 + c, r1 = pv[k0 + c];
-        int a = -1, bb = -1;
-        for (int q = 0; q < cnt; ++q) {
-          if (lrow[q] == r0) a = q;
-          if (lrow[q] == r1) bb = q;
-        }
-        if (a < 0) { lrow[cnt] = r0; lsrc[cnt] = r0; a = cnt++; }
-        if (bb < 0) { lrow[cnt] = r1; lsrc[cnt] = r1; bb = cnt++; }
-        const int tmp = lsrc[a];
-        lsrc[a] = lsrc[bb];
-        lsrc[bb] = tmp;
-      }
-      nl = cnt;
-    }
-    __syncthreads();
-    const int L = nl;
+    // 2. the other columns, 64 at a time
     const int ntrail = n - b;
     for (int j0 = 0; j0 < ntrail; j0 += CH) {
       const int nc = min(CH, ntrail - j0);
-      // (a) old values of the touched rows of the chunk's columns
-      for (int q = t; q < L * CH; q += NT) {
-        const int l = q / CH, jc = q % CH;
-        if (jc < nc) {
+      for (int q = t; q < B * CH; q += NT) {
+        const int c = q / CH, jc = q % CH;
+        float v = 0.0f;
+        if (c < b && jc < nc) {
           const int j = j0 + jc < k0 ? j0 + jc : j0 + jc + b;
-          OLD[(size_t)l * CH + jc] = Ag[(long long)j * n + lsrc[l]];
+          v = Ag[(long long)j * n + pi[k0 + c]];
         }
+        U[q] = v;
       }
       __syncthreads();
-      // (b) the gathered rows U (panel rows after the interchanges) and x~ in place
-      for (int q = t; q < L * CH; q += NT) {
-        const int l = q / CH, jc = q % CH;
-        if (jc < nc) {
-          const int j = j0 + jc < k0 ? j0 + jc : j0 + jc + b;
-          const int row = lrow[l];
-          const float v = OLD[(size_t)l * CH + jc];
-          if (row >= k0 && row < k0 + b) {
-            U[(size_t)(row - k0) * CH + jc] = v;
-            Ag[(long long)j * n + row] = 0.0f;
-          } else {
-            Ag[(long long)j * n + row] = v;
-          }
-        }
-      }
-      // (every panel row k0 + c is in the list: step c interchanges it, possibly with itself)
-      for (int q = t; q < (B - b) * CH; q += NT) U[(size_t)b * CH + q] = 0.0f;   // unused rows of U
-      __syncthreads();
-      // (c) C += P U on the chunk: 4 x 4 tiles (rows 4 r .. 4 r + 3, chunk columns 4 s .. 4 s + 3)
       const int rt = (n + 3) / 4, ntile = rt * (CH / 4);
       for (int tile = t; tile < ntile; tile += NT) {
         const int r = tile % rt, sc = tile / rt;
         const int i0 = 4 * r, c0 = 4 * sc;
         if (c0 >= nc) continue;
+        bool live[4];
+#pragma unroll
+        for (int qr = 0; qr < 4; ++qr) live[qr] = i0 + qr < n && !mask[i0 + qr];
         float acc[4][4];
 #pragma unroll
         for (int qc = 0; qc < 4; ++qc) {
@@ -669,7 +815,7 @@ __global__ void __launch_bounds__(GJG_NT, 2) k_gj_global(long long E, int n, flo
           const int j = j0 + jc < k0 ? j0 + jc : j0 + jc + b;
 #pragma unroll
           for (int qr = 0; qr < 4; ++qr)
-            acc[qc][qr] = (jc < nc && i0 + qr < n) ? Ag[(long long)j * n + i0 + qr] : 0.0f;
+            acc[qc][qr] = (jc < nc && live[qr]) ? Ag[(long long)j * n + i0 + qr] : 0.0f;
         }
 #pragma unroll 8
         for (int k = 0; k < B; ++k) {
@@ -694,13 +840,29 @@ __global__ void __launch_bounds__(GJG_NT, 2) k_gj_global(long long E, int n, flo
       }
       __syncthreads();
     }
+    for (int c = t; c < b; c += NT) mask[pi[k0 + c]] = 0;
+    __syncthreads();
+  }
+  // every column in logical row order, B columns at a time through shared memory
+  float* colbuf = P;                           // [B][np]
+  for (int j0 = 0; j0 < n; j0 += B) {
+    const int w = min(B, n - j0);
+    for (int q = t; q < w * n; q += NT) {
+      const int jj = q / n, i = q - jj * n;
+      colbuf[(size_t)jj * np + i] = Ag[(long long)(j0 + jj) * n + i];
+    }
+    __syncthreads();
+    for (int q = t; q < w * n; q += NT) {
+      const int jj = q / n, i = q - jj * n;
+      Ag[(long long)(j0 + jj) * n + i] = colbuf[(size_t)jj * np + pi[i]];
+    }
+    __syncthreads();
   }
   // columns back in reverse pivot order: the composed interchange gives each column's final
   // position dest; the block is rewritten in strips of 32 rows through shared memory, each strip
-  // read whole before it is written, so the permutation is in place without a scratch block
-  int* cur = lrow;                             // [n] (the interchange lists are no longer needed)
-  int* dest = cur + n;
+  // read whole before it is written
   if (t == 0) {
+    int* cur = mask;                           // (the mask is no longer needed)
     for (int i = 0; i < n; ++i) cur[i] = i;
     for (int k = n - 1; k >= 0; --k) {
       const int q = cur[k];
@@ -1196,11 +1358,15 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
     cudaFuncSetAttribute(k_gj_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem);
     k_gj_inverse<true><<<(unsigned)m->E, 256, gj_smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
   } else if (nb <= 768) {
+    // one row per thread (320 threads) up to n = 320, with the unrolled panel steps; two rows per
+    // thread up to 640; three (256 threads) up to 768
+    const int NT = nb <= 640 ? 320 : 256;
     const int np = ((nb + 3) & ~3) + 4;
-    const size_t smem = sizeof(float) * ((size_t)GJG_B * np + (size_t)GJG_B * GJG_CH + 2 * GJG_B * GJG_CH) +
-                        sizeof(int) * ((size_t)nb + std::max<size_t>(4 * GJG_B, 2 * (size_t)nb));
-    cudaFuncSetAttribute(k_gj_global<GJG_B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gj_global<GJG_B><<<(unsigned)m->E, GJG_NT, smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+    const size_t smem = sizeof(float) * ((size_t)GJG_B * np + (size_t)GJG_B * GJG_CH + 2 * (NT / 32 + 1) * GJG_B) +
+                        sizeof(int) * 4 * (size_t)nb;
+    auto kern = nb <= 320 ? k_gj_global<GJG_B, 1, 320> : (nb <= 640 ? k_gj_global<GJG_B, 2, 320> : k_gj_global<GJG_B, 3, 256>);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(unsigned)m->E, NT, smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
   } else {
     k_gj_inverse<false><<<(unsigned)m->E, 256, sizeof(float) * 2 * nb, s>>>(m->E, nb, S->blocks, S->piv, S->info);
   }
