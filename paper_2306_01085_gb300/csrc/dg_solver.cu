@@ -1354,7 +1354,14 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
   if (rc) return rc;
   prof_begin(m, s, KK_LU);
   const size_t gj_smem = sizeof(float) * (2 * nb + (size_t)nb * nb);
-  if (gj_smem <= 200 * 1024) {
+  if (nb > 64 && nb <= 160) {
+    // blocked, one row per thread (160 threads): several blocks per SM overlap their panel steps
+    const int np = ((nb + 3) & ~3) + 4;
+    const size_t smem = sizeof(float) * ((size_t)GJG_B * np + (size_t)GJG_B * GJG_CH + 2 * (160 / 32 + 1) * GJG_B) +
+                        sizeof(int) * 4 * (size_t)nb;
+    cudaFuncSetAttribute(k_gj_global<GJG_B, 1, 160>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gj_global<GJG_B, 1, 160><<<(unsigned)m->E, 160, smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+  } else if (gj_smem <= 200 * 1024) {
     cudaFuncSetAttribute(k_gj_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem);
     k_gj_inverse<true><<<(unsigned)m->E, 256, gj_smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
   } else if (nb <= 768) {
