@@ -145,6 +145,23 @@ int dg_mesh_sizes(const dg_mesh* mesh, int64_t* n_elem, int32_t* n_p, int64_t* n
 int dg_mesh_nodes(const dg_mesh* mesh, double* x, void* stream);
 
 /*
+ * How the FP64 evaluations (dg_gradient, dg_residual, dg_jvp with DG_JV_EXACT, the FP64 solver
+ * paths) form the Gauss values and face traces of u from its nodal values (Sec. 3.1: the nodes ->
+ * quadrature points map B x B x B and the extrapolation to the faces):
+ *   DG_INTERP_FP64: sum-factorised 1D passes in FP64 arithmetic on the CUDA cores;
+ *   DG_INTERP_TC:   one dense contraction per element on the tensor cores (tcgen05, FP16 operands
+ *                   with FP32 accumulation), FP64-accurate by error-free slicing: both operands
+ *                   rounded to 47 bits relative to their row / column maximum and split into six
+ *                   base-256 digits; digit products of level <= 5 accumulated exactly; the error is
+ *                   below 1e-12 of each variable's largest nodal value in its element.
+ * The mode applies to later calls on this mesh (not stream-ordered: set it between evaluations).
+ * Errors: DG_EINVAL for an unknown mode.
+ */
+#define DG_INTERP_FP64 0
+#define DG_INTERP_TC   1
+int dg_mesh_set_interp(dg_mesh* mesh, int32_t mode);
+
+/*
  * LDG gradient, Eq. DGformulation (first equation): q solves (q, p) = -(u, div p) + <u_hat, p.n>
  * for every p in Q_h, with u_hat = (u + u^-)/2 on interior faces and the boundary traces of
  * DG_BC_*. Output q is nodal, layout [n_elem][3][5][n_p]. u and q must not overlap.

@@ -145,6 +145,10 @@ struct dg_mesh {
   float* w32_base = nullptr;
   dg::Mlp* mlp = nullptr;           // learned preconditioner, created by dg_mlp_init
   double* static_scratch = nullptr; // device address of dg_residual_static's array on this device
+  int interp_mode = DG_INTERP_FP64; // DG_INTERP_*: how the FP64 paths form Gauss values and traces
+  uint16_t* tc_aslices = nullptr;   // tensor-core interpolation: operator digit slices (first use)
+  int* tc_rowexp = nullptr;         //   their row exponents
+  int* tc_err = nullptr;            //   set when a bounded wait of the kernel gave up
 };
 
 void dg_mlp_release(dg_mesh* m);
@@ -160,6 +164,12 @@ std::vector<double> radial_layers(double r_in, double r_out, int nz, double h1);
 // device address of dg_residual_static's scratch array on the current device dev (looked up once
 // per device; the lookup loads the module that holds the array)
 int static_scratch_address(int dev, double** out);
+// nodal -> Gauss values and face traces of NC planes (u, and v for NC = 2) on the tensor cores,
+// FP64-accurate (dg_tc_interp.cu); ug / uf as k_interp's outputs, plane 0 at the given pointers
+template <int N, int NC>
+int interp_tc(dg_mesh* m, const double* u, const double* v, double* ug, double* uf, cudaStream_t s);
+int interp_tc_prepare(dg_mesh* m);   // the operator's digit slices (allocates once per mesh)
+void interp_tc_release(dg_mesh* m);
 }
 int mlp_setup(dg_mesh* mesh, const double* u, double dt_aii, cudaStream_t s);
 // J_G v = M v - c J_r(u) v in one tangent pass (exact tangent; FP32 arithmetic when f32). With

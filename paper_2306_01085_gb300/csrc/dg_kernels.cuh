@@ -1130,6 +1130,8 @@ static int set_smem(K kernel, size_t bytes) {
 template <int N, int NC, typename R = double, int CM = CM_NATIVE>
 static int run_interp(dg_mesh* m, const double* u, const double* v, cudaStream_t s) {
   constexpr int EPB = Epb<N, NC>::value, NP = Shape<N>::NP;
+  if constexpr (std::is_same<R, double>::value && CM == CM_NATIVE)
+    if (m->interp_mode == DG_INTERP_TC) return interp_tc<N, NC>(m, u, v, m->ws.ug, m->ws.uf, s);
   const size_t sm = Smem<N, NC, R>::interp;
   int rc = set_smem(k_interp<N, NC, R, CM>, sm);
   if (rc) return rc;
@@ -1162,6 +1164,9 @@ static int run_grad(dg_mesh* m, cudaStream_t s) {
 template <int N, typename R>
 static int run_interp_tangent(dg_mesh* m, const double* v, cudaStream_t s) {
   constexpr int EPB = Epb<N, 1>::value, NP = Shape<N>::NP, NF = Shape<N>::NF;
+  if constexpr (std::is_same<R, double>::value)
+    if (m->interp_mode == DG_INTERP_TC)
+      return interp_tc<N, 1>(m, v, nullptr, m->ws.ug + m->E * 5 * NP, m->ws.uf + m->E * 30 * NF, s);
   const size_t sm = Smem<N, 1, R>::interp;
   int rc = set_smem(k_interp<N, 1, R, CM_NATIVE>, sm);
   if (rc) return rc;

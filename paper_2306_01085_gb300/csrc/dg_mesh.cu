@@ -321,6 +321,7 @@ static void free_mesh(dg_mesh* m) {
   prof_release(m);
   dg_solver_release(m);
   dg_mlp_release(m);
+  dg::interp_tc_release(m);
   if (m->w32_base) cudaFree(m->w32_base);
   void* ptrs[] = {m->d_ops, m->x, m->geo, m->acc, m->xg, m->fgeo, m->mixg, m->mixf, m->nbr, m->nbr_fo, m->face_e,
                   m->face_f,
@@ -557,6 +558,21 @@ extern "C" int dg_mesh_nodes(const dg_mesh* mesh, double* x, void* stream) {
   if (!mesh || !x) return fail(DG_EINVAL, "dg_mesh_nodes: null argument");
   DG_CUDA_TRY(cudaMemcpyAsync(x, mesh->x, sizeof(double) * mesh->E * 3 * mesh->np, cudaMemcpyDeviceToDevice,
                               (cudaStream_t)stream));
+  return DG_OK;
+}
+
+extern "C" int dg_mesh_set_interp(dg_mesh* mesh, int32_t mode) {
+  if (!mesh) return fail(DG_EINVAL, "dg_mesh_set_interp: null mesh");
+  if (mode != DG_INTERP_FP64 && mode != DG_INTERP_TC) return fail(DG_EINVAL, "dg_mesh_set_interp: unknown mode");
+  if (mode == DG_INTERP_TC) {
+    int dev = 0;
+    DG_CUDA_TRY(cudaGetDevice(&dev));
+    DG_CUDA_TRY(cudaSetDevice(mesh->device));
+    const int rc = dg::interp_tc_prepare(mesh);
+    cudaSetDevice(dev);
+    if (rc) return rc;
+  }
+  mesh->interp_mode = mode;
   return DG_OK;
 }
 

@@ -18,6 +18,8 @@ HEADER = os.path.join(HERE, "..", "include", "dg.h")
 
 DG_JV_EXACT = 0
 DG_JV_FD = 1
+DG_INTERP_FP64 = 0
+DG_INTERP_TC = 1
 
 
 class DgMeshDesc(ctypes.Structure):
@@ -87,6 +89,7 @@ def lib():
     L.dg_mesh_destroy.restype = None
     L.dg_mesh_sizes.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_int32), i64p]
     L.dg_mesh_nodes.argtypes = [vp, dp, vp]
+    L.dg_mesh_set_interp.argtypes = [vp, i32]
     L.dg_gradient.argtypes = [vp, dp, dp, vp]
     L.dg_residual.argtypes = [vp, dp, dp, d, dp, vp]
     L.dg_jvp.argtypes = [vp, dp, dp, d, i32, d, dp, dp, vp]
@@ -198,6 +201,15 @@ class Mesh:
     def empty(self, shape=None):
         import torch
         return torch.empty(shape or self.u_shape, dtype=torch.float64, device="cuda")
+
+    def set_interp(self, mode):
+        """'fp64' (sum-factorised FP64 passes) or 'tc' (tensor-core contraction with FP64-accurate
+        digit slicing) for the nodes -> Gauss values and face traces step of the FP64 paths."""
+        modes = {"fp64": DG_INTERP_FP64, "tc": DG_INTERP_TC}
+        if mode not in modes:
+            raise DgError(f"unknown interpolation mode {mode!r}")
+        _check(lib().dg_mesh_set_interp(self._h, modes[mode]))
+        self.interp = mode
 
     def nodes(self):
         x = self.empty((self.n_elem, 3, self.n_p))

@@ -42,7 +42,7 @@ def grad_err_per_var(q, q_ref, u, om):
     return err / scale
 
 
-def run_pair(torch, desc, seed=1, t=0.0, check_fd=True):
+def run_pair(torch, desc, seed=1, t=0.0, check_fd=True, interp="fp64"):
     from paper_2306_01085_gb300.dg import Mesh
     om = OM.OracleMesh(desc)
     u = W.state_for(desc, om.X, seed)
@@ -51,6 +51,7 @@ def run_pair(torch, desc, seed=1, t=0.0, check_fd=True):
     r_ref = OD.residual(om, u, q_ref, t)
     jv_ref = OD.jvp(om, u, v, t)
     m = Mesh(desc, nodes=om.X)
+    m.set_interp(interp)
     ug = torch.from_numpy(u).cuda()
     vg = torch.from_numpy(v).cuda()
     q = m.gradient(ug)
@@ -177,3 +178,84 @@ def test_library_mesh_generator_matches_workload_mesh(torch_cuda, name):
     x = m.nodes().cpu().numpy()
     m.close()
     assert np.abs(x - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# The tensor-core interpolation (DG_INTERP_TC): nodes -> Gauss values and face traces as one dense
+# contraction per element on tcgen05, FP64-accurate by digit slicing. Same bar against the oracle.
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_tc_interp_box_walls_ragged(torch_cuda, p):
+    """27 elements: a partial last group of 6 (NC = 2) and 12 (NC = 1) elements for every p."""
+    d = W.box_desc(p=p, n=3, bc_lo=W.BC_WALL, bc_hi=W.BC_OUTFLOW, visc_exp=0.69, re=40.0)
+    assert_parity(run_pair(torch_cuda, d, seed=3, check_fd=False, interp="tc"))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_tc_interp_shell_small(torch_cuda, p):
+    d = W.shell_desc(n=3, nr=2, p=p, euv=True)
+    d.h_first = 0.0
+    d.euv_r_peak = 0.5 * (d.r_inner + d.r_outer)
+    d.euv_width = 0.25 * (d.r_outer - d.r_inner)
+    assert_parity(run_pair(torch_cuda, d, seed=5, t=0.3, check_fd=False, interp="tc"))
+
+
+def test_tc_interp_single_element(torch_cuda):
+    assert_parity(run_pair(torch_cuda, W.box_desc(p=4, n=1), seed=7, check_fd=False, interp="tc"))
+
+
+def test_tc_interp_full_size(torch_cuda):
+    """The 12,288-element p = 4 shell in the benchmark's launch configuration: the tensor-core
+    path against the oracle on sampled elements (1e-12) and against the FP64 path everywhere
+    (1e-13 per variable), residual and Jv."""
+    torch = torch_cuda
+    from paper_2306_01085_gb300.dg import Mesh
+    desc = W.CONFIGS["shell16x8_p4"][0]()
+    om = OM.OracleMesh(desc)
+    u = W.state_for(desc, om.X, 4)
+    v = W.unit_vector(104, u.shape)
+    rng = np.random.default_rng(1)
+    sample = np.unique(np.concatenate([rng.choice(om.n_elem, 12, replace=False), [0, om.n_elem - 1]]))
+    r_ref = OD.residual(om, u, None, 0.0, elems=sample)
+    jv_ref = OD.jvp(om, u, v, 0.0, elems=sample)
+    m = Mesh(desc, nodes=om.X)
+    ug = torch.from_numpy(u).cuda()
+    vg = torch.from_numpy(v).cuda()
+    out = {}
+    for mode in ("fp64", "tc"):
+        m.set_interp(mode)
+        r = torch.empty_like(ug)
+        jv = m.jvp(ug, vg, t=0.0, r_out=r)
+        out[mode] = (r.cpu().numpy(), jv.cpu().numpy())
+    m.close()
+    r_tc, jv_tc = out["tc"]
+    assert np.all(rel_err_per_var(r_tc[sample], r_ref, 1) <= TOL)
+    assert np.all(rel_err_per_var(jv_tc[sample], jv_ref, 1) <= TOL)
+    assert np.all(rel_err_per_var(r_tc, out["fp64"][0], 1) <= 1e-13)
+    assert np.all(rel_err_per_var(jv_tc, out["fp64"][1], 1) <= 1e-13)
+
+
+def test_tc_interp_propagates_nan(torch_cuda):
+    """A NaN nodal value makes its element's Gauss values NaN, as in the FP64 passes: the residual's
+    NaN pattern is the same in both modes (the solver's NaN checks see it)."""
+    torch = torch_cuda
+    from paper_2306_01085_gb300.dg import Mesh
+    d = W.box_desc(p=3, n=3)
+    m = Mesh(d)
+    u = torch.from_numpy(W.state_for(d, m.nodes().cpu().numpy(), 2)).cuda()
+    u[13, 4, 7] = float("nan")
+    masks = []
+    for mode in ("fp64", "tc"):
+        m.set_interp(mode)
+        masks.append(torch.isnan(m.residual(u)).cpu().numpy())
+    m.close()
+    assert masks[0].any() and np.array_equal(masks[0], masks[1])
+
+
+def test_tc_interp_mode_is_validated(torch_cuda):
+    from paper_2306_01085_gb300.dg import DgError, Mesh, lib
+    m = Mesh(W.box_desc(p=2, n=2))
+    assert lib().dg_mesh_set_interp(m._h, 7) == -1
+    with pytest.raises(DgError):
+        m.set_interp("bf16")
+    m.close()
