@@ -460,7 +460,9 @@ typedef struct dg_radial_stats {
 /* Build the ensemble on the current device. node_r: optional HOST array [n_elem][p+1] of the node
  * radii (NULL: geometric layers from desc); params: HOST array [n_col][4] = (epsilon, alpha0,
  * latitude, longitude [rad]), read during the call. Allocates the library storage (synchronises).
- * Errors: DG_EINVAL (sizes, p, boundaries, non-positive radii or alpha0), DG_ENOMEM, DG_ECUDA. */
+ * Errors: DG_EINVAL (sizes, p, boundaries, non-positive radii or alpha0, more than 6000 unknowns
+ * 3 (p+1) n_elem per column: the banded solve keeps a column's right-hand side in shared memory),
+ * DG_ENOMEM, DG_ECUDA. */
 int dg_radial_create(const dg_radial_desc* desc, const double* node_r, const double* params, dg_radial** out);
 void dg_radial_destroy(dg_radial* rad);
 

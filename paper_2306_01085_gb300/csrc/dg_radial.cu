@@ -531,7 +531,7 @@ __global__ void k_rvol(int E, long long nc, ROps<R> O, RPhys<R> P, RGeo<R> g, RP
       for (int i = 0; i < N; ++i) {
         const int row = k * 3 * N + c * N + i;
         const R val = ((kp == k && c == pr.var) ? Mcol[i] : R(0)) - stage_c * Rn[c][i].d;
-        band[((long long)(KL + KU + row - jcol) * n + jcol) * nc + col] = (float)val;
+        band[((long long)col * n + jcol) * Band<N>::LD + (KL + KU + row - jcol)] = (float)val;
       }
   } else {
 #pragma unroll
@@ -550,78 +550,269 @@ __global__ void k_rvol(int E, long long nc, ROps<R> O, RPhys<R> P, RGeo<R> g, RP
 }
 
 // ------------------------------------------------------------------------------------------------
-// banded LU with partial pivoting (the unblocked LAPACK gbtf2 algorithm), one thread per column
+// banded LU with partial pivoting (the unblocked LAPACK gbtf2 algorithm), one warp per column
 // ------------------------------------------------------------------------------------------------
+// Band storage per column (system) col, column-contiguous: entry (rb, j) of the LAPACK band at
+// ab[(col n + j) LD + rb], i.e. matrix entry (j - KV + rb, j) with KV = KL + KU; ipiv[col n + j].
+// The lanes take the rows j + i (i = lane + 32 r) of step j, so every load and store of a column is
+// contiguous across the warp. The pivot column stays in registers from the search to the scaling;
+// the columns to the right are updated in batches of RB_COLS, all of a batch's entries loaded
+// before any is stored, and the row interchange of each column is a pair of shuffles. The
+// arithmetic (pivot choice, scaling, x - l p per entry in the same order) is that of the
+// one-thread-per-column algorithm.
+constexpr int RB_COLS = 16;
+
 template <int N>
-__global__ void k_rband_lu(int n, long long nc, float* __restrict__ ab, int* __restrict__ ipiv, int* __restrict__ info) {
-  constexpr int KL = Band<N>::KL, KU = Band<N>::KU, KV = KL + KU;
-  const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= nc) return;
-  auto A = [&](int rb, int j) -> float& { return ab[((long long)rb * n + j) * nc + col]; };
+__global__ void __launch_bounds__(128) k_rband_lu(int n, long long nc, float* __restrict__ ab, int* __restrict__ ipiv,
+                                                  int* __restrict__ info) {
+  constexpr int KL = Band<N>::KL, KU = Band<N>::KU, KV = KL + KU, LD = Band<N>::LD;
+  constexpr int RP = (KL + 1 + 31) / 32;        // rows 0 .. KL of a step per lane
+  const int lane = threadIdx.x & 31;
+  const long long col = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (col >= nc) return;                        // whole warps
+  float* A0 = ab + col * (long long)n * LD;
+  int* pv = ipiv + col * (long long)n;
   int ju = 0;
   int bad = 0;
   for (int j = 0; j < n; ++j) {
     const int km = min(KL, n - 1 - j);
-    int jp = 0;
-    float amax = fabsf(A(KV, j));
-    for (int i = 1; i <= km; ++i) {
-      const float a = fabsf(A(KV + i, j));
-      if (a > amax) {
-        amax = a;
-        jp = i;
+    float* Aj = A0 + (long long)j * LD + KV;     // Aj[i]: row j + i of column j
+    float v[RP];
+    float best = -1.0f;
+    int bi = 0;
+    bool nan = false;
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      const int i = lane + 32 * r;
+      v[r] = i <= km ? Aj[i] : 0.0f;
+      const float a = fabsf(v[r]);
+      nan |= i <= km && a != a;
+      if (i <= km && a > best) {
+        best = a;
+        bi = i;
       }
     }
-    ipiv[(long long)j * nc + col] = j + jp;
-    if (amax == 0.0f || !isfinite(amax)) {
+    for (int off = 16; off > 0; off >>= 1) {
+      const float o = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (o > best || (o == best && oi < bi)) {
+        best = o;
+        bi = oi;
+      }
+    }
+    nan = __any_sync(0xffffffffu, nan);
+    const int jp = bi, jl = jp & 31, jr = jp >> 5;
+    if (lane == 0) pv[j] = j + jp;
+    if (nan || best == 0.0f || !isfinite(best)) {
       bad = 1;
       continue;
     }
     ju = max(ju, min(j + KU + jp, n - 1));
-    if (jp != 0)
-      for (int c = j; c <= ju; ++c) {
-        float& x = A(KV + jp - (c - j), c);
-        float& y = A(KV - (c - j), c);
-        const float tmp = x;
-        x = y;
-        y = tmp;
-      }
-    const float inv = 1.0f / A(KV, j);
-    for (int i = 1; i <= km; ++i) A(KV + i, j) *= inv;
-    for (int c = j + 1; c <= ju; ++c) {
-      const float p = A(KV - (c - j), c);
-      if (p != 0.0f)
-        for (int i = 1; i <= km; ++i) A(KV + i - (c - j), c) -= A(KV + i, j) * p;
+    // column j: rows 0 and jp interchanged, the pivot kept, the rest scaled by its reciprocal
+    const float v0 = __shfl_sync(0xffffffffu, v[0], 0);
+    float vp = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      const float t = __shfl_sync(0xffffffffu, v[r], jl);
+      if (jr == r) vp = t;
     }
+    const float inv = 1.0f / vp;
+    float l[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      const int i = lane + 32 * r;
+      const float x = i == jp ? v0 : (i == 0 ? vp : v[r]);
+      l[r] = i == 0 ? 0.0f : x * inv;
+      if (i <= km) Aj[i] = i == 0 ? x : l[r];
+    }
+    // columns j + 1 .. ju
+    for (int c0 = j + 1; c0 <= ju; c0 += RB_COLS) {
+      float x[RB_COLS][RP];
+#pragma unroll
+      for (int q = 0; q < RB_COLS; ++q) {
+        const int c = c0 + q;
+        const float* Ac = A0 + (long long)c * LD + KV - (c - j);   // Ac[i]: row j + i of column c
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const int i = lane + 32 * r;
+          x[q][r] = (c <= ju && i <= km) ? Ac[i] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RB_COLS; ++q) {
+        const int c = c0 + q;
+        if (c > ju) break;
+        float xp = 0.0f;
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const float t = __shfl_sync(0xffffffffu, x[q][r], jl);
+          if (jr == r) xp = t;
+        }
+        const float x0 = __shfl_sync(0xffffffffu, x[q][0], 0);
+        // rows 0 and jp interchanged: the new row 0 (the multiplier's partner p) is the old row jp
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const int i = lane + 32 * r;
+          if (i == 0) x[q][r] = xp;
+          else if (i == jp) x[q][r] = x0;
+        }
+        const float pc = xp;
+        if (pc != 0.0f) {
+#pragma unroll
+          for (int r = 0; r < RP; ++r) {
+            const int i = lane + 32 * r;
+            if (i >= 1) x[q][r] = x[q][r] - l[r] * pc;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RB_COLS; ++q) {
+        const int c = c0 + q;
+        float* Ac = A0 + (long long)c * LD + KV - (c - j);
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const int i = lane + 32 * r;
+          if (c <= ju && i <= km) Ac[i] = x[q][r];
+        }
+      }
+    }
+    __syncwarp();
   }
-  if (bad) atomicOr(info, 1);
+  if (bad && lane == 0) atomicOr(info, 1);
 }
 
-// solve L U x = b in place on b (FP64 [n][nc] rows of the element-major ordering), FP32 arithmetic
+// solve L U x = b in place on b (FP64 [n][nc] rows of the element-major ordering), FP32 products
+// accumulated in float-float pairs (hi + lo, about 48 bits: the accuracy of the former FP64
+// accumulation without the FP64 pipe, which issues 2 lanes per SM per cycle on this GPU); one warp
+// per column with the column's b in shared memory ([warps][n] pairs). The band is read in blocks of
+// SB_STEPS steps, the next block's loads issued before the current block is applied.
+constexpr int SB_STEPS = 8;
+
+// (hi, lo) -= p: Knuth's two-sum of hi and -p, the low parts added, then renormalised
+__device__ __forceinline__ void ff_sub(float& hi, float& lo, float p) {
+  const float s = hi - p;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (-p - bb);
+  const float t = e + lo;
+  hi = s + t;
+  lo = t - (hi - s);
+}
+
 template <int N>
-__global__ void k_rband_solve(int n, long long nc, const float* __restrict__ ab, const int* __restrict__ ipiv,
-                              double* __restrict__ b) {
-  constexpr int KL = Band<N>::KL, KU = Band<N>::KU, KV = KL + KU;
-  const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= nc) return;
-  auto A = [&](int rb, int j) -> float { return ab[((long long)rb * n + j) * nc + col]; };
-  auto B = [&](int i) -> double& { return b[(long long)i * nc + col]; };
-  for (int j = 0; j < n; ++j) {
-    const int km = min(KL, n - 1 - j);
-    const int l = ipiv[(long long)j * nc + col];
-    if (l != j) {
-      const double t = B(l);
-      B(l) = B(j);
-      B(j) = t;
+__global__ void __launch_bounds__(128) k_rband_solve(int n, long long nc, const float* __restrict__ ab,
+                                                     const int* __restrict__ ipiv, double* __restrict__ b) {
+  constexpr int KL = Band<N>::KL, KU = Band<N>::KU, KV = KL + KU, LD = Band<N>::LD;
+  constexpr int RPT = (KL + 31) / 32, RPB = (KV + 31) / 32;
+  extern __shared__ float2 sb_all[];
+  const int lane = threadIdx.x & 31;
+  const long long col = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (col >= nc) return;                        // whole warps; no block barrier below
+  float2* sb = sb_all + (size_t)(threadIdx.x >> 5) * n;
+  for (int i = lane; i < n; i += 32) {
+    const double x = b[(long long)i * nc + col];
+    const float hi = (float)x;
+    sb[i] = make_float2(hi, (float)(x - (double)hi));
+  }
+  const float* A0 = ab + col * (long long)n * LD;
+  const int* pv = ipiv + col * (long long)n;
+  // forward: L y = P b
+  float a[SB_STEPS][RPT], an[SB_STEPS][RPT];
+  int lp[SB_STEPS], lpn[SB_STEPS];
+  auto load_lower = [&](int j0, float (&dst)[SB_STEPS][RPT], int (&pd)[SB_STEPS]) {
+#pragma unroll
+    for (int s = 0; s < SB_STEPS; ++s) {
+      const int j = j0 + s;
+      const int km = j < n ? min(KL, n - 1 - j) : -1;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = 1 + lane + 32 * r;
+        dst[s][r] = i <= km ? A0[(long long)j * LD + KV + i] : 0.0f;
+      }
+      pd[s] = j < n ? pv[j] : j;
     }
-    const float bj = (float)B(j);
-    for (int i = 1; i <= km; ++i) B(j + i) -= (double)(A(KV + i, j) * bj);
+  };
+  load_lower(0, a, lp);
+  __syncwarp();
+  for (int j0 = 0; j0 < n; j0 += SB_STEPS) {
+    if (j0 + SB_STEPS < n) load_lower(j0 + SB_STEPS, an, lpn);
+#pragma unroll
+    for (int s = 0; s < SB_STEPS; ++s) {
+      const int j = j0 + s;
+      if (j >= n) break;
+      const int km = min(KL, n - 1 - j);
+      const int l = lp[s];
+      if (l != j) {
+        if (lane == 0) {
+          const float2 t = sb[l];
+          sb[l] = sb[j];
+          sb[j] = t;
+        }
+        __syncwarp();
+      }
+      const float bj = sb[j].x;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = 1 + lane + 32 * r;
+        if (i <= km) {
+          float2 y = sb[j + i];
+          ff_sub(y.x, y.y, __fmul_rn(a[s][r], bj));   // the rounded product, never fused
+          sb[j + i] = y;
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int s = 0; s < SB_STEPS; ++s) {
+      lp[s] = lpn[s];
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) a[s][r] = an[s][r];
+    }
   }
-  for (int j = n - 1; j >= 0; --j) {
-    const float bj = (float)B(j) / A(KV, j);
-    B(j) = bj;
-    const int lm = min(j, KV);
-    for (int i = 1; i <= lm; ++i) B(j - i) -= (double)(A(KV - i, j) * bj);
+  // backward: U x = y, steps j = n - 1 .. 0 in blocks
+  float u[SB_STEPS][RPB], un[SB_STEPS][RPB], d[SB_STEPS], dn[SB_STEPS];
+  auto load_upper = [&](int j0, float (&dst)[SB_STEPS][RPB], float (&dd)[SB_STEPS]) {
+#pragma unroll
+    for (int s = 0; s < SB_STEPS; ++s) {
+      const int j = j0 - s;
+      const int lm = j >= 0 ? min(j, KV) : -1;
+#pragma unroll
+      for (int r = 0; r < RPB; ++r) {
+        const int i = 1 + lane + 32 * r;
+        dst[s][r] = i <= lm ? A0[(long long)j * LD + KV - i] : 0.0f;
+      }
+      dd[s] = j >= 0 ? A0[(long long)j * LD + KV] : 1.0f;
+    }
+  };
+  load_upper(n - 1, u, d);
+  for (int j0 = n - 1; j0 >= 0; j0 -= SB_STEPS) {
+    if (j0 - SB_STEPS >= 0) load_upper(j0 - SB_STEPS, un, dn);
+#pragma unroll
+    for (int s = 0; s < SB_STEPS; ++s) {
+      const int j = j0 - s;
+      if (j < 0) break;
+      const int lm = min(j, KV);
+      const float bj = sb[j].x / d[s];
+      __syncwarp();                              // every lane has read sb[j]
+      if (lane == 0) sb[j] = make_float2(bj, 0.0f);
+#pragma unroll
+      for (int r = 0; r < RPB; ++r) {
+        const int i = 1 + lane + 32 * r;
+        if (i <= lm) {
+          float2 y = sb[j - i];
+          ff_sub(y.x, y.y, __fmul_rn(u[s][r], bj));
+          sb[j - i] = y;
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int s = 0; s < SB_STEPS; ++s) {
+      d[s] = dn[s];
+#pragma unroll
+      for (int r = 0; r < RPB; ++r) u[s][r] = un[s][r];
+    }
   }
+  for (int i = lane; i < n; i += 32) b[(long long)i * nc + col] = (double)sb[i].x + (double)sb[i].y;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -761,8 +952,8 @@ struct dg_radial {
   // implicit step
   float* qp = nullptr;       // [1 + probes][4][E][N][nc]
   float* fp = nullptr;       // [1 + probes][3][E+1][nc]
-  float* band = nullptr;     // [LD][n][nc]
-  int* ipiv = nullptr;       // [n][nc]
+  float* band = nullptr;     // [nc][n][LD]: LAPACK band storage of each column's stage Jacobian
+  int* ipiv = nullptr;       // [nc][n]
   int* info = nullptr;
   double *U0 = nullptr, *known = nullptr, *R1 = nullptr, *R2 = nullptr, *rr = nullptr, *G = nullptr;
   double *norms = nullptr, *g0 = nullptr, *ratio = nullptr, *ratio_h = nullptr;
@@ -871,7 +1062,7 @@ int jacobian_lu(dg_radial* m, const double* U, double t, double c, cudaStream_t 
   DG_LAUNCH_CHECK("k_rprobe");
   DG_CUDA_TRY(cudaMemsetAsync(m->info, 0, sizeof(int), s));
   rprof_begin(m, s, RK_LU);
-  k_rband_lu<N><<<blocks_for(nc), kThreads, 0, s>>>(n, nc, m->band, m->ipiv, m->info);
+  k_rband_lu<N><<<blocks_for(32 * nc), kThreads, 0, s>>>(n, nc, m->band, m->ipiv, m->info);
   rprof_end(m, s);
   DG_LAUNCH_CHECK("k_rband_lu");
   return DG_OK;
@@ -880,7 +1071,9 @@ int jacobian_lu(dg_radial* m, const double* U, double t, double c, cudaStream_t 
 template <int N>
 int solve_t(dg_radial* m, double* b, cudaStream_t s) {
   rprof_begin(m, s, RK_SOLVE);
-  k_rband_solve<N><<<blocks_for(m->nc), kThreads, 0, s>>>(m->n, m->nc, m->band, m->ipiv, b);
+  const size_t smem = sizeof(float2) * (size_t)(kThreads / 32) * m->n;
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_rband_solve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_rband_solve<N><<<blocks_for(32 * m->nc), kThreads, smem, s>>>(m->n, m->nc, m->band, m->ipiv, b);
   rprof_end(m, s);
   DG_LAUNCH_CHECK("k_rband_solve");
   return DG_OK;
@@ -1037,6 +1230,8 @@ extern "C" int dg_radial_create(const dg_radial_desc* desc, const double* node_r
   const dg_radial_desc& d = *desc;
   if (d.p < 1 || d.p > 4) return fail(DG_EINVAL, "dg_radial_create: p must be in 1..4");
   if (d.n_elem < 1 || d.n_col < 1) return fail(DG_EINVAL, "dg_radial_create: sizes must be positive");
+  if ((long long)d.n_elem * 3 * (d.p + 1) > 6000)
+    return fail(DG_EINVAL, "dg_radial_create: at most 6000 unknowns per variable set of a column (3 (p+1) n_elem)");
   if (!(d.r_inner > 0 && d.r_outer > d.r_inner)) return fail(DG_EINVAL, "dg_radial_create: need r_outer > r_inner > 0");
   if ((d.bc_lo != DG_BC_WALL && d.bc_lo != DG_BC_OUTFLOW) || (d.bc_hi != DG_BC_WALL && d.bc_hi != DG_BC_OUTFLOW))
     return fail(DG_EINVAL, "dg_radial_create: boundaries must be wall or outflow");
