@@ -273,7 +273,8 @@ typedef struct dg_solver_opts {
     int32_t precond_refresh; /* DG_REFRESH_* */
     int32_t jv_mode;         /* DG_JV_EXACT or DG_JV_FD for the GMRES operator */
     int32_t jv_prec;         /* DG_PREC_F64, or DG_PREC_F32 (mixed): FP32 inner Jv, block assembly and
-                                Gram-Schmidt arithmetic on the FP64 Krylov basis */
+                                Gram-Schmidt arithmetic; the Krylov basis is stored in FP32 when
+                                gmres_restart <= 31 and gmres_rtol >= 1e-6 (FP64 otherwise) */
     double newton_rtol;      /* stop when ||G||_2 <= newton_rtol ||G(U^0)||_2 (1e-8) */
     double gmres_rtol;       /* each Newton system to ||b - J x|| <= gmres_rtol ||b|| (1e-3) */
     double abs_floor;        /* or when ||G||_2 <= abs_floor ||M U||_2 (1e-14) */

@@ -438,6 +438,129 @@ __global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot_f32(long long n2,
   }
 }
 
+// The same two sweeps on an FP32-stored basis (the mixed-precision solve keeps its Krylov vectors
+// in FP32: the basis is read three times per Arnoldi step, and the projections are FP32 anyway).
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS, 2) k_mdot_f32v(long long n2, const float2* __restrict__ V, long long ldv2,
+                                                          const double2* __restrict__ w, double* __restrict__ partial) {
+  float acc[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j] = 0.0f;
+  double nrm = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double2 x = w[i];
+    const float xx = to_f32(x.x), xy = to_f32(x.y);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float2 v = V[j * ldv2 + i];
+      acc[j] = fmaf(v.x, xx, fmaf(v.y, xy, acc[j]));
+    }
+    nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+  }
+  __shared__ double red[RED_THREADS / 32][K + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    double v = to_f64(acc[j]);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][j] = v;
+  }
+  for (int off = 16; off > 0; off >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, off);
+  if (lane == 0) red[warp][K] = nrm;
+  __syncthreads();
+  for (int j = threadIdx.x; j <= K; j += blockDim.x) {
+    double v = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) v += red[q][j];
+    partial[j * RED_BLOCKS + blockIdx.x] = v;
+  }
+}
+
+template <int K, bool DOTS>
+__global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot_f32v(long long n2, const float2* __restrict__ V,
+                                                                   long long ldv2, const double* __restrict__ h,
+                                                                   double2* __restrict__ w, double* __restrict__ partial) {
+  __shared__ float hs[K];
+  if (threadIdx.x < K) hs[threadIdx.x] = to_f32(h[threadIdx.x]);
+  __syncthreads();
+  constexpr int NA = DOTS ? K : 1;
+  constexpr bool CACHE = DOTS && K <= 24;
+  float acc[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) acc[j] = 0.0f;
+  double nrm = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    double2 x = w[i];
+    float2 vf[CACHE ? K : 1];
+    float cx = 0.0f, cy = 0.0f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float2 f = V[j * ldv2 + i];
+      if constexpr (CACHE) vf[j] = f;
+      cx = fmaf(hs[j], f.x, cx);
+      cy = fmaf(hs[j], f.y, cy);
+    }
+    x.x -= to_f64(cx);
+    x.y -= to_f64(cy);
+    w[i] = x;
+    if constexpr (DOTS) {
+      const float xx = to_f32(x.x), xy = to_f32(x.y);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        float2 f;
+        if constexpr (CACHE) f = vf[j];
+        else f = __ldcg(&V[j * ldv2 + i]);   // the element was just read: an L2 hit
+        acc[j] = fmaf(f.x, xx, fmaf(f.y, xy, acc[j]));
+      }
+    }
+    nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+  }
+  __shared__ double red[RED_THREADS / 32][NA + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if constexpr (DOTS) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      double a = to_f64(acc[j]);
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+      if (lane == 0) red[warp][j] = a;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, off);
+  if (lane == 0) red[warp][NA] = nrm;
+  __syncthreads();
+  for (int j = threadIdx.x; j < (DOTS ? K + 1 : 1); j += blockDim.x) {
+    const int src = DOTS ? j : NA;
+    double a = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) a += red[q][src];
+    partial[j * RED_BLOCKS + blockIdx.x] = a;
+  }
+}
+
+// out = a x in FP32 (a new basis vector), and the FP32 vector widened back to FP64
+__global__ void k_scale_to_f32(long long n, const double* __restrict__ x, double a, const double* __restrict__ den,
+                               float* __restrict__ out) {
+  const float sf = den ? (float)(1.0 / sqrt(*den)) : (float)a;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = to_f32(x[i]) * sf;
+}
+
+__global__ void k_widen(long long n, const float* __restrict__ x, double* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = to_f64(x[i]);
+}
+
+// out = sum_j y[j] V_j (j < k) on the FP32 basis, FP32 sums widened to FP64
+__global__ void k_combine_f32v(long long n, int k, const float* __restrict__ V, long long ldv,
+                               const double* __restrict__ y, double* __restrict__ out) {
+  __shared__ float ys[MAXK];
+  if (threadIdx.x < k) ys[threadIdx.x] = (float)y[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    for (int j = 0; j < k; ++j) v = fmaf(ys[j], V[j * ldv + i], v);
+    out[i] = to_f64(v);
+  }
+}
+
 // out[j] = sum_b partial[j][b] (+= into out when accumulate); also out_sq = partial[k] sum
 __global__ void k_mdot_finish(int k, const double* __restrict__ partial, double* __restrict__ out, int accumulate) {
   const int j = threadIdx.x;
@@ -1268,6 +1391,35 @@ static void update_dot(long long n, int k, const double* V, const double* h, dou
 #undef DG_UD
 }
 
+// the two sweeps on the FP32 basis (k <= 32 vectors, n even)
+static void mdot_f32v(long long n, int k, const float* V, const double* w, double* partial, cudaStream_t s) {
+  const long long n2 = n / 2;
+  const float2* V2 = reinterpret_cast<const float2*>(V);
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  switch (k) {
+#define DG_MDV(K) \
+  case K: k_mdot_f32v<K><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V2, n2, w2, partial); return;
+    DG_K_CASES1(DG_MDV)
+#undef DG_MDV
+  }
+}
+
+static void update_dot_f32v(long long n, int k, const float* V, const double* h, double* w, double* partial, bool dots,
+                            cudaStream_t s) {
+  const long long n2 = n / 2;
+  const float2* V2 = reinterpret_cast<const float2*>(V);
+  double2* w2 = reinterpret_cast<double2*>(w);
+  switch (k) {
+#define DG_UDV(K)                                                                                    \
+  case K:                                                                                            \
+    if (dots) k_update_dot_f32v<K, true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V2, n2, h, w2, partial);   \
+    else k_update_dot_f32v<K, false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V2, n2, h, w2, partial);       \
+    return;
+    DG_K_CASES1(DG_UDV)
+#undef DG_UDV
+  }
+}
+
 // J_G v = M v - c J_r(U) v
 static int stage_matvec(dg_mesh* m, Solver* S, const double* U, double t, double c, int jv_mode, int jv_prec,
                         const double* v, double* out, cudaStream_t s, bool value_ready = false) {
@@ -1695,6 +1847,9 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
   }
   std::vector<double> H((size_t)(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
   const bool f32gs = o.jv_prec == DG_PREC_F32;
+  // the mixed-precision solve stores its Krylov basis in FP32 (in the same allocation)
+  const bool f32basis = f32gs && n % 2 == 0 && R + 1 <= 32 && o.gmres_rtol >= 1e-6;
+  float* Vf = reinterpret_cast<float*>(V);
   for (int cycle = 0; cycle < o.max_restarts; ++cycle) {
     // r = b - A x
     if (cycle == 0) {
@@ -1710,14 +1865,23 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
     if (rc) return rc;
     if (!std::isfinite(beta)) return fail(DG_ENAN, "GMRES: non-finite residual");
     if (beta <= o.gmres_rtol * bnorm) return DG_OK;
-    k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0 / beta, r, 0.0, nullptr, 0.0, nullptr, V);
+    if (f32basis) k_scale_to_f32<<<grid_for(n), 256, 0, s>>>(n, r, 1.0 / beta, nullptr, Vf);
+    else k_lincomb<<<grid_for(n), 256, 0, s>>>(n, 1.0 / beta, r, 0.0, nullptr, 0.0, nullptr, V);
     DG_LAUNCH_CHECK("k_lincomb");
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int kdone = 0;
     bool converged = false;
     for (int k = 0; k < R; ++k) {
-      rc = precond_apply(m, S, o.precond, V + (long long)k * n, z, s);
+      if (f32basis) {
+        prof_begin(m, s, KK_BLAS);
+        k_widen<<<grid_for(n), 256, 0, s>>>(n, Vf + (long long)k * n, S->v(VTMP));
+        prof_end(m, s);
+        DG_LAUNCH_CHECK("k_widen");
+        rc = precond_apply(m, S, o.precond, S->v(VTMP), z, s);
+      } else {
+        rc = precond_apply(m, S, o.precond, V + (long long)k * n, z, s);
+      }
       if (rc) return rc;
       rc = stage_matvec(m, S, U, t, c, o.jv_mode, o.jv_prec, z, w, s, vr);
       if (rc) return rc;
@@ -1726,13 +1890,23 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
       // below the Krylov tolerance), the basis, the subtraction from w and the norms stay FP64.
       prof_begin(m, s, KK_BLAS);
       // h1 = V^T w; w -= V h1 fused with h2 = V^T w; w -= V h2 fused with |w|^2
-      mdot(n, k + 1, V, w, S->partial, s, f32gs);
-      k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev, 0);
-      update_dot(n, k + 1, V, S->hdev, w, S->partial, true, s, f32gs);
-      k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev + MAXK, 0);
-      update_dot(n, k + 1, V, S->hdev + MAXK, w, S->partial, false, s, f32gs);
-      k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev + MAXK + k + 1, 0);
-      k_scale_dev<<<grid_for(n), 256, 0, s>>>(n, w, S->hdev + MAXK + k + 1, V + (long long)(k + 1) * n);
+      if (f32basis) {
+        mdot_f32v(n, k + 1, Vf, w, S->partial, s);
+        k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev, 0);
+        update_dot_f32v(n, k + 1, Vf, S->hdev, w, S->partial, true, s);
+        k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev + MAXK, 0);
+        update_dot_f32v(n, k + 1, Vf, S->hdev + MAXK, w, S->partial, false, s);
+        k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev + MAXK + k + 1, 0);
+        k_scale_to_f32<<<grid_for(n), 256, 0, s>>>(n, w, 0.0, S->hdev + MAXK + k + 1, Vf + (long long)(k + 1) * n);
+      } else {
+        mdot(n, k + 1, V, w, S->partial, s, f32gs);
+        k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev, 0);
+        update_dot(n, k + 1, V, S->hdev, w, S->partial, true, s, f32gs);
+        k_mdot_finish<<<1, MAXK, 0, s>>>(k, S->partial, S->hdev + MAXK, 0);
+        update_dot(n, k + 1, V, S->hdev + MAXK, w, S->partial, false, s, f32gs);
+        k_mdot_finish<<<1, MAXK, 0, s>>>(0, S->partial, S->hdev + MAXK + k + 1, 0);
+        k_scale_dev<<<grid_for(n), 256, 0, s>>>(n, w, S->hdev + MAXK + k + 1, V + (long long)(k + 1) * n);
+      }
       prof_end(m, s);
       DG_LAUNCH_CHECK("arnoldi");
       DG_CUDA_TRY(cudaMemcpyAsync(S->hhost, S->hdev, sizeof(double) * 2 * MAXK, cudaMemcpyDeviceToHost, s));
@@ -1767,7 +1941,8 @@ static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U
     }
     std::memcpy(S->hhost, y.data(), sizeof(double) * kdone);
     DG_CUDA_TRY(cudaMemcpyAsync(S->hdev, S->hhost, sizeof(double) * kdone, cudaMemcpyHostToDevice, s));
-    k_combine<<<grid_for(n), 256, 0, s>>>(n, kdone, V, n, S->hdev, r);
+    if (f32basis) k_combine_f32v<<<grid_for(n), 256, 0, s>>>(n, kdone, Vf, n, S->hdev, r);
+    else k_combine<<<grid_for(n), 256, 0, s>>>(n, kdone, V, n, S->hdev, r);
     DG_LAUNCH_CHECK("k_combine");
     rc = precond_apply(m, S, o.precond, r, z, s);
     if (rc) return rc;
