@@ -510,7 +510,7 @@ __global__ void k_rvol(int E, long long nc, ROps<R> O, RPhys<R> P, RGeo<R> g, RP
   }
   if constexpr (PROBE) {
     // column (kp, var, node) of J_G = M - stage_c J_r in the rows of element k
-    constexpr int KL = Band<N>::KL;
+    constexpr int KL = Band<N>::KL, KU = Band<N>::KU;  // band offsets of the probe column
     const int n = 3 * N * E;
     const int jcol = kp * 3 * N + pr.var * N + pr.node;
     R Mcol[N];
@@ -531,7 +531,7 @@ __global__ void k_rvol(int E, long long nc, ROps<R> O, RPhys<R> P, RGeo<R> g, RP
       for (int i = 0; i < N; ++i) {
         const int row = k * 3 * N + c * N + i;
         const R val = ((kp == k && c == pr.var) ? Mcol[i] : R(0)) - stage_c * Rn[c][i].d;
-        band[((long long)col * n + row) * Band<N>::LD + (KL + jcol - row)] = (float)val;
+        band[((long long)col * n + jcol) * Band<N>::LD + (KL + KU + row - jcol)] = (float)val;
       }
   } else {
 #pragma unroll
@@ -552,33 +552,31 @@ __global__ void k_rvol(int E, long long nc, ROps<R> O, RPhys<R> P, RGeo<R> g, RP
 // ------------------------------------------------------------------------------------------------
 // banded LU with partial pivoting (the unblocked LAPACK gbtf2 algorithm), one warp per column
 // ------------------------------------------------------------------------------------------------
-// Row-oriented band storage per column (system) col: matrix row r keeps the columns r - KL ..
-// r + KU + KL (the upper band widened by the fill of the row interchanges) at
-// ab[(col n + r) LD + (c - r + KL)]; the multipliers of step j sit where column j's entries below the
-// diagonal were. ipiv[col n + j].
-// Step j: the lanes take the rows j + i of column j for the pivot search and the multipliers, then
-// the columns c = j + 1 .. ju for the interchange and the update, so the rows' entries of one update
-// row are contiguous across the warp and each lane applies every row's l p to its own columns with
-// all loads in flight before the stores. The arithmetic (pivot choice, scaling, x - l p per entry)
-// is that of the one-thread-per-column algorithm.
+// Band storage per column (system) col, column-contiguous: entry (rb, j) of the LAPACK band at
+// ab[(col n + j) LD + rb], i.e. matrix entry (j - KV + rb, j) with KV = KL + KU; ipiv[col n + j].
+// The lanes take the rows j + i (i = lane + 32 r) of step j, so every load and store of a column is
+// contiguous across the warp. The pivot column stays in registers from the search to the scaling;
+// the columns to the right are updated in batches of RB_COLS, all of a batch's entries loaded
+// before any is stored, and the row interchange of each column is a pair of shuffles. The
+// arithmetic (pivot choice, scaling, x - l p per entry in the same order) is that of the
+// one-thread-per-column algorithm.
+constexpr int RB_COLS = 16;
+
 template <int N>
 __global__ void __launch_bounds__(128) k_rband_lu(int n, long long nc, float* __restrict__ ab, int* __restrict__ ipiv,
                                                   int* __restrict__ info) {
   constexpr int KL = Band<N>::KL, KU = Band<N>::KU, KV = KL + KU, LD = Band<N>::LD;
   constexpr int RP = (KL + 1 + 31) / 32;        // rows 0 .. KL of a step per lane
-  constexpr int CPL = (KV + 1 + 31) / 32;       // columns j .. j + KV per lane
-  __shared__ float sl_all[4][KL + 1];            // the multipliers of the step, per warp
   const int lane = threadIdx.x & 31;
   const long long col = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (col >= nc) return;                        // whole warps
-  float* sl = sl_all[(threadIdx.x >> 5) & 3];
   float* A0 = ab + col * (long long)n * LD;
-  auto at = [&](int r, int c) -> float& { return A0[(long long)r * LD + (c - r + KL)]; };
   int* pv = ipiv + col * (long long)n;
   int ju = 0;
   int bad = 0;
   for (int j = 0; j < n; ++j) {
     const int km = min(KL, n - 1 - j);
+    float* Aj = A0 + (long long)j * LD + KV;     // Aj[i]: row j + i of column j
     float v[RP];
     float best = -1.0f;
     int bi = 0;
@@ -586,7 +584,7 @@ __global__ void __launch_bounds__(128) k_rband_lu(int n, long long nc, float* __
 #pragma unroll
     for (int r = 0; r < RP; ++r) {
       const int i = lane + 32 * r;
-      v[r] = i <= km ? at(j + i, j) : 0.0f;
+      v[r] = i <= km ? Aj[i] : 0.0f;
       const float a = fabsf(v[r]);
       nan |= i <= km && a != a;
       if (i <= km && a > best) {
@@ -610,20 +608,6 @@ __global__ void __launch_bounds__(128) k_rband_lu(int n, long long nc, float* __
       continue;
     }
     ju = max(ju, min(j + KU + jp, n - 1));
-    // rows j and j + jp interchanged in the columns j + 1 .. ju (column j is rewritten below)
-    if (jp != 0) {
-#pragma unroll
-      for (int t = 0; t < CPL; ++t) {
-        const int c = j + 1 + lane + 32 * t;
-        if (c <= ju) {
-          float& x = at(j, c);
-          float& y = at(j + jp, c);
-          const float a = x;
-          x = y;
-          y = a;
-        }
-      }
-    }
     // column j: rows 0 and jp interchanged, the pivot kept, the rest scaled by its reciprocal
     const float v0 = __shfl_sync(0xffffffffu, v[0], 0);
     float vp = 0.0f;
@@ -633,30 +617,64 @@ __global__ void __launch_bounds__(128) k_rband_lu(int n, long long nc, float* __
       if (jr == r) vp = t;
     }
     const float inv = 1.0f / vp;
+    float l[RP];
 #pragma unroll
     for (int r = 0; r < RP; ++r) {
       const int i = lane + 32 * r;
-      if (i <= km) {
-        const float x = i == jp ? v0 : (i == 0 ? vp : v[r]);
-        const float y = i == 0 ? x : x * inv;
-        at(j + i, j) = y;
-        sl[i] = y;
-      }
+      const float x = i == jp ? v0 : (i == 0 ? vp : v[r]);
+      l[r] = i == 0 ? 0.0f : x * inv;
+      if (i <= km) Aj[i] = i == 0 ? x : l[r];
     }
-    __syncwarp();
-    // rows j + 1 .. j + km of the columns j + 1 .. ju: x - l p, p the column's entry in row j
+    // columns j + 1 .. ju
+    for (int c0 = j + 1; c0 <= ju; c0 += RB_COLS) {
+      float x[RB_COLS][RP];
 #pragma unroll
-    for (int t = 0; t < CPL; ++t) {
-      const int c = j + 1 + lane + 32 * t;
-      if (c > ju) continue;
-      const float pc = at(j, c);
-      if (pc == 0.0f) continue;
-      float x[KL];
+      for (int q = 0; q < RB_COLS; ++q) {
+        const int c = c0 + q;
+        const float* Ac = A0 + (long long)c * LD + KV - (c - j);   // Ac[i]: row j + i of column c
 #pragma unroll
-      for (int i = 1; i <= KL; ++i) x[i - 1] = i <= km ? at(j + i, c) : 0.0f;
+        for (int r = 0; r < RP; ++r) {
+          const int i = lane + 32 * r;
+          x[q][r] = (c <= ju && i <= km) ? Ac[i] : 0.0f;
+        }
+      }
 #pragma unroll
-      for (int i = 1; i <= KL; ++i)
-        if (i <= km) at(j + i, c) = x[i - 1] - sl[i] * pc;
+      for (int q = 0; q < RB_COLS; ++q) {
+        const int c = c0 + q;
+        if (c > ju) break;
+        float xp = 0.0f;
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const float t = __shfl_sync(0xffffffffu, x[q][r], jl);
+          if (jr == r) xp = t;
+        }
+        const float x0 = __shfl_sync(0xffffffffu, x[q][0], 0);
+        // rows 0 and jp interchanged: the new row 0 (the multiplier's partner p) is the old row jp
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const int i = lane + 32 * r;
+          if (i == 0) x[q][r] = xp;
+          else if (i == jp) x[q][r] = x0;
+        }
+        const float pc = xp;
+        if (pc != 0.0f) {
+#pragma unroll
+          for (int r = 0; r < RP; ++r) {
+            const int i = lane + 32 * r;
+            if (i >= 1) x[q][r] = x[q][r] - l[r] * pc;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RB_COLS; ++q) {
+        const int c = c0 + q;
+        float* Ac = A0 + (long long)c * LD + KV - (c - j);
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const int i = lane + 32 * r;
+          if (c <= ju && i <= km) Ac[i] = x[q][r];
+        }
+      }
     }
     __syncwarp();
   }
@@ -708,7 +726,7 @@ __global__ void __launch_bounds__(128) k_rband_solve(int n, long long nc, const 
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         const int i = 1 + lane + 32 * r;
-        dst[s][r] = i <= km ? A0[(long long)(j + i) * LD + KL - i] : 0.0f;   // L(j + i, j)
+        dst[s][r] = i <= km ? A0[(long long)j * LD + KV + i] : 0.0f;
       }
       pd[s] = j < n ? pv[j] : j;
     }
@@ -760,9 +778,9 @@ __global__ void __launch_bounds__(128) k_rband_solve(int n, long long nc, const 
 #pragma unroll
       for (int r = 0; r < RPB; ++r) {
         const int i = 1 + lane + 32 * r;
-        dst[s][r] = i <= lm ? A0[(long long)(j - i) * LD + KL + i] : 0.0f;   // U(j - i, j)
+        dst[s][r] = i <= lm ? A0[(long long)j * LD + KV - i] : 0.0f;
       }
-      dd[s] = j >= 0 ? A0[(long long)j * LD + KL] : 1.0f;                      // U(j, j)
+      dd[s] = j >= 0 ? A0[(long long)j * LD + KV] : 1.0f;
     }
   };
   load_upper(n - 1, u, d);
@@ -934,7 +952,7 @@ struct dg_radial {
   // implicit step
   float* qp = nullptr;       // [1 + probes][4][E][N][nc]
   float* fp = nullptr;       // [1 + probes][3][E+1][nc]
-  float* band = nullptr;     // [nc][n][LD]: each column's stage Jacobian by rows, band columns r - KL .. r + KU + KL
+  float* band = nullptr;     // [nc][n][LD]: LAPACK band storage of each column's stage Jacobian
   int* ipiv = nullptr;       // [nc][n]
   int* info = nullptr;
   double *U0 = nullptr, *known = nullptr, *R1 = nullptr, *R2 = nullptr, *rr = nullptr, *G = nullptr;
