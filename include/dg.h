@@ -258,6 +258,10 @@ int dg_residual_static(dg_mesh* mesh, const double* u, double t, double* r, void
 #define DG_REFRESH_STEP   0  /* build the preconditioner once per step, at u_n */
 #define DG_REFRESH_STAGE  1  /* rebuild at the start of every stage */
 #define DG_REFRESH_NEWTON 2  /* rebuild at every Newton iteration */
+#define DG_REFRESH_LAGGED 3  /* build at u_n of one step and reuse it for the next refresh_every - 1
+                                steps (a lagged preconditioner: the operator changes little over a
+                                step); rebuilt sooner when the kind, the precision, dt a_11 or the
+                                mesh's solver storage changes, and after a failed step */
 
 #define DG_PREC_F64 0
 #define DG_PREC_F32 1
@@ -280,6 +284,8 @@ typedef struct dg_solver_opts {
     double abs_floor;        /* or when ||G||_2 <= abs_floor ||M U||_2 (1e-14) */
     int32_t rb_size;         /* DG_PC_RB*: Newton updates kept in the reduced basis, 1..16 (8) */
     int32_t flags;           /* DG_OPT_* bits (0) */
+    int32_t refresh_every;   /* DG_REFRESH_LAGGED: steps served by one preconditioner build, >= 1 (3) */
+    int32_t reserved;        /* zero */
 } dg_solver_opts;
 
 /* dg_solver_opts.flags: recompute the state's Gauss values, traces and LDG gradient in every

@@ -1218,6 +1218,10 @@ struct Solver {
   float* hscale = nullptr;     // [E][5Np]: their power-of-two column scales
   int hld = 0;
   bool bj16_ready = false;
+  // DG_REFRESH_LAGGED: what the current preconditioner was built for and how many steps it served
+  bool lag_valid = false;
+  int lag_kind = -1, lag_prec = -1, lag_steps = 0;
+  double lag_caii = 0.0;
   // reduced basis (Sec. 3.2): ring of the last Newton updates, orthonormal basis W, Z = J_G W,
   // Y = P0^{-1} Z - W, C = (W^T P0^{-1} Z)^{-1} on the device, Gram Z^T Z on the host
   int rb_cap = 0, rb_count = 0, rb_head = 0, rb_r = 0, rb_kind = 0;
@@ -1813,6 +1817,7 @@ static int rb_build(dg_mesh* m, Solver* S, int kind, const double* U, double t, 
 
 // (re)build the preconditioner of kind at state U
 static int pc_setup(dg_mesh* m, Solver* S, int kind, const double* U, double t, double c, cudaStream_t s, bool f32) {
+  S->lag_valid = false;   // a lagged preconditioner is only reused as its own step built it
   if (kind == DG_PC_BJ || kind == DG_PC_RB_BJ) return bj_setup(m, S, U, t, c, s, f32);
   if (kind == DG_PC_BJ16) return bj_setup(m, S, U, t, c, s, f32, true);
   if (kind == DG_PC_MLP) return mlp_setup(m, U, c, s);
@@ -1971,6 +1976,7 @@ extern "C" void dg_solver_opts_default(dg_solver_opts* o) {
   o->gmres_rtol = 1e-3;
   o->abs_floor = 1e-14;
   o->rb_size = 8;
+  o->refresh_every = 3;
 }
 
 extern "C" int dg_precond_setup(dg_mesh* mesh, int32_t kind, const double* u, double t, double dt_aii,
@@ -2045,6 +2051,9 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
   if (rc) return rc;
   if (o.max_newton < 1 || o.max_restarts < 1) return fail(DG_EINVAL, "dg_implicit_step: bad limits");
   if (o.precond < DG_PC_NONE || o.precond > DG_PC_BJ16) return fail(DG_EINVAL, "dg_implicit_step: unknown precond");
+  if (o.precond_refresh < DG_REFRESH_STEP || o.precond_refresh > DG_REFRESH_LAGGED ||
+      (o.precond_refresh == DG_REFRESH_LAGGED && o.refresh_every < 1))
+    return fail(DG_EINVAL, "dg_implicit_step: bad preconditioner refresh");
   const bool rb = o.precond == DG_PC_RB || o.precond == DG_PC_RB_BJ;
   Solver* S = nullptr;
   rc = solver_get(mesh, o.gmres_restart, &S);
@@ -2072,16 +2081,31 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
   DG_CUDA_TRY(cudaMemcpyAsync(U, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   double* Mun = S->v(VTMP);
   auto finish = [&](int code) {
+    if (code != DG_OK) S->lag_valid = false;   // a failed step rebuilds its preconditioner next time
     st.status = code;
     st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = st;
     return code;
   };
-  if (o.precond != DG_PC_NONE && o.precond_refresh == DG_REFRESH_STEP) {
+  bool build_now = o.precond != DG_PC_NONE && o.precond_refresh == DG_REFRESH_STEP;
+  if (o.precond != DG_PC_NONE && o.precond_refresh == DG_REFRESH_LAGGED) {
+    build_now = !(S->lag_valid && S->lag_kind == o.precond && S->lag_prec == o.jv_prec &&
+                  S->lag_caii == dt * A[0][0] && S->lag_steps < o.refresh_every);
+    if (build_now) S->lag_valid = false;
+    else ++S->lag_steps;
+  }
+  if (build_now) {
     const auto p0 = std::chrono::steady_clock::now();
     rc = pc_setup(mesh, S, o.precond, un, t + c[0] * dt, dt * A[0][0], s, o.jv_prec == DG_PREC_F32);
     st.precond_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p0).count();
     if (rc) return finish(rc);
+    if (o.precond_refresh == DG_REFRESH_LAGGED) {
+      S->lag_valid = true;
+      S->lag_kind = o.precond;
+      S->lag_prec = o.jv_prec;
+      S->lag_caii = dt * A[0][0];
+      S->lag_steps = 1;
+    }
   }
   for (int i = 0; i < o.stages; ++i) {
     const double ti = t + c[i] * dt, ci = dt * A[i][i];

@@ -48,7 +48,7 @@ class DgSolverOpts(ctypes.Structure):
         ("max_newton", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_refresh", ctypes.c_int32),
         ("jv_mode", ctypes.c_int32), ("jv_prec", ctypes.c_int32), ("newton_rtol", ctypes.c_double),
         ("gmres_rtol", ctypes.c_double), ("abs_floor", ctypes.c_double), ("rb_size", ctypes.c_int32),
-        ("flags", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("refresh_every", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -61,7 +61,7 @@ class DgStepStats(ctypes.Structure):
 
 
 PC = {"none": 0, "bj": 1, "mlp": 2, "rb": 3, "rb_bj": 4, "bj16": 5}
-REFRESH = {"step": 0, "stage": 1, "newton": 2}
+REFRESH = {"step": 0, "stage": 1, "newton": 2, "lagged": 3}
 
 _lib = None
 

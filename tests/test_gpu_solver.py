@@ -223,6 +223,46 @@ def test_solver_variants_reach_the_same_state(torch_cuda):
     assert all(r[0]["status"] == 0 for r in runs.values())
 
 
+def test_lagged_preconditioner_refresh(torch_cuda):
+    """DG_REFRESH_LAGGED builds the FP16 block-Jacobi preconditioner on the first of every
+    refresh_every steps and reuses it in between (no setup time on those steps); a change of dt or
+    a failed step forces a build; every step still converges to the Newton tolerance, so the
+    states follow the per-step builds to that tolerance."""
+    torch = torch_cuda
+    from paper_2306_01085_gb300.dg import DgError, Mesh
+    d = W.shell_desc(n=3, nr=6, p=2, euv=True)
+    m = Mesh(d)
+    u0 = torch.from_numpy(W.state_for(d, m.nodes().cpu().numpy(), 8)).cuda()
+    dt = 60.0 / W.shell_reference().t0
+    kw = dict(stages=3, precond="bj16", jv_prec="f32", newton_rtol=1e-10, gmres_rtol=1e-4)
+    u_ref, u_lag = u0.clone(), u0.clone()
+    built = []
+    for k in range(4):
+        m.implicit_step(u_ref, k * dt, dt, **kw)
+    for k in range(4):   # (the per-step builds above leave no lagged preconditioner: the first step builds)
+        st = m.implicit_step(u_lag, k * dt, dt, precond_refresh="lagged", refresh_every=2, **kw)
+        built.append(st["precond_ms"] > 0)
+    assert built == [True, False, True, False], built
+    du = np.abs(u_ref.cpu().numpy() - u0.cpu().numpy()).max(axis=(0, 2))
+    diff = np.abs(u_lag.cpu().numpy() - u_ref.cpu().numpy()).max(axis=(0, 2))
+    assert np.all(diff <= 1e-6 * du), (diff, du)
+    # dt changes: build; then reuse
+    st = m.implicit_step(u_lag, 4 * dt, 0.5 * dt, precond_refresh="lagged", refresh_every=3, **kw)
+    assert st["precond_ms"] > 0
+    st = m.implicit_step(u_lag, 4.5 * dt, 0.5 * dt, precond_refresh="lagged", refresh_every=3, **kw)
+    assert st["precond_ms"] == 0
+    # a failed step (Newton capped at one iteration) leaves the state and forces the next build
+    before = u_lag.clone()
+    st = m.implicit_step(u_lag, 5 * dt, 0.5 * dt, precond_refresh="lagged", refresh_every=3, check=False,
+                         **dict(kw, newton_rtol=1e-14, max_newton=1))
+    assert st["rc"] == -4 and torch.equal(u_lag, before)
+    st = m.implicit_step(u_lag, 5 * dt, 0.5 * dt, precond_refresh="lagged", refresh_every=3, **kw)
+    assert st["status"] == 0 and st["precond_ms"] > 0
+    with pytest.raises(DgError):
+        m.implicit_step(u_lag, 0.0, dt, precond_refresh="lagged", refresh_every=0, **kw)
+    m.close()
+
+
 @pytest.mark.parametrize("p", [2, 3])
 @pytest.mark.parametrize("jv_prec", ["f64", "f32"])
 def test_value_plane_once_per_solve_is_bit_identical(torch_cuda, jv_prec, p):
