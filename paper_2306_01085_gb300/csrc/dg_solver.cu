@@ -982,8 +982,8 @@ __global__ void __launch_bounds__(NT, 2) k_gj_global(long long E, int n, float* 
     __syncthreads();
   }
   // columns back in reverse pivot order: the composed interchange gives each column's final
-  // position dest; the block is rewritten in strips of 32 rows through shared memory, each strip
-  // read whole before it is written
+  // position dest; the block is rewritten in strips of SR rows through shared memory, each strip
+  // read whole before it is written (the strip, [n][SR], fits the panel buffer's B np floats)
   if (t == 0) {
     int* cur = mask;                           // (the mask is no longer needed)
     for (int i = 0; i < n; ++i) cur[i] = i;
@@ -995,16 +995,17 @@ __global__ void __launch_bounds__(NT, 2) k_gj_global(long long E, int n, float* 
     for (int i = 0; i < n; ++i) dest[cur[i]] = i;
   }
   __syncthreads();
-  float* strip = P;                            // [n][32] (n 32 <= B np floats)
-  for (int r0 = 0; r0 < n; r0 += 32) {
-    const int rows = min(32, n - r0);
-    for (int q = t; q < n * 32; q += NT) {
-      const int j = q >> 5, rr = q & 31;
+  constexpr int SR = B < 32 ? B : 32;
+  float* strip = P;                            // [n][SR]
+  for (int r0 = 0; r0 < n; r0 += SR) {
+    const int rows = min(SR, n - r0);
+    for (int q = t; q < n * SR; q += NT) {
+      const int j = q / SR, rr = q % SR;
       if (rr < rows) strip[q] = Ag[(long long)j * n + r0 + rr];
     }
     __syncthreads();
-    for (int q = t; q < n * 32; q += NT) {
-      const int j = q >> 5, rr = q & 31;
+    for (int q = t; q < n * SR; q += NT) {
+      const int j = q / SR, rr = q % SR;
       if (rr < rows) Ag[(long long)dest[j] * n + r0 + rr] = strip[q];
     }
     __syncthreads();
