@@ -1511,30 +1511,36 @@ static int bj_setup(dg_mesh* m, Solver* S, const double* U, double t, double c, 
   if (rc) return rc;
   prof_begin(m, s, KK_LU);
   const size_t gj_smem = sizeof(float) * (2 * nb + (size_t)nb * nb);
-  if (nb > 64 && nb <= 160) {
-    // blocked, one row per thread (160 threads): several blocks per SM overlap their panel steps
+  // blocked kernels: panel width B, MRT rows per thread, NT threads; the shared memory holds the
+  // panel [B][np], a chunk of the other columns [B][GJG_CH], the pivot slots and four index arrays
+  auto gj_blocked = [&](auto kern, int B, int NT) -> int {
     const int np = ((nb + 3) & ~3) + 4;
-    const size_t smem = sizeof(float) * ((size_t)GJG_B * np + (size_t)GJG_B * GJG_CH + 2 * (160 / 32 + 1) * GJG_B) +
+    const size_t smem = sizeof(float) * ((size_t)B * np + (size_t)B * GJG_CH + 2 * (NT / 32 + 1) * (size_t)B) +
                         sizeof(int) * 4 * (size_t)nb;
-    cudaFuncSetAttribute(k_gj_global<GJG_B, 1, 160>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gj_global<GJG_B, 1, 160><<<(unsigned)m->E, 160, smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+    DG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)m->E, NT, smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+    return DG_OK;
+  };
+  // panel widths measured per size: 16 for 135^2 (98,304 blocks: 56 ms against 68 ms at 32), 24
+  // for 320^2 (221,184 blocks: 1.03 s against 1.17 s), 32 above
+  if (nb > 64 && nb <= 160) {
+    // one row per thread (160 threads): several blocks per SM overlap their panel steps
+    rc = gj_blocked(k_gj_global<16, 1, 160>, 16, 160);
   } else if (gj_smem <= 200 * 1024) {
     cudaFuncSetAttribute(k_gj_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem);
     k_gj_inverse<true><<<(unsigned)m->E, 256, gj_smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+  } else if (nb <= 320) {
+    // one row per thread (320 threads), the panel steps unrolled
+    rc = gj_blocked(k_gj_global<24, 1, 320>, 24, 320);
+  } else if (nb <= 640) {
+    rc = gj_blocked(k_gj_global<GJG_B, 2, 320>, GJG_B, 320);   // two rows per thread
   } else if (nb <= 768) {
-    // one row per thread (320 threads) up to n = 320, with the unrolled panel steps; two rows per
-    // thread up to 640; three (256 threads) up to 768
-    const int NT = nb <= 640 ? 320 : 256;
-    const int np = ((nb + 3) & ~3) + 4;
-    const size_t smem = sizeof(float) * ((size_t)GJG_B * np + (size_t)GJG_B * GJG_CH + 2 * (NT / 32 + 1) * GJG_B) +
-                        sizeof(int) * 4 * (size_t)nb;
-    auto kern = nb <= 320 ? k_gj_global<GJG_B, 1, 320> : (nb <= 640 ? k_gj_global<GJG_B, 2, 320> : k_gj_global<GJG_B, 3, 256>);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<(unsigned)m->E, NT, smem, s>>>(m->E, nb, S->blocks, S->piv, S->info);
+    rc = gj_blocked(k_gj_global<GJG_B, 3, 256>, GJG_B, 256);   // three rows per thread
   } else {
     k_gj_inverse<false><<<(unsigned)m->E, 256, sizeof(float) * 2 * nb, s>>>(m->E, nb, S->blocks, S->piv, S->info);
   }
   prof_end(m, s);
+  if (rc) return rc;
   DG_LAUNCH_CHECK("k_gj_inverse");
   int info = 0;
   DG_CUDA_TRY(cudaMemcpyAsync(&info, S->info, sizeof(int), cudaMemcpyDeviceToHost, s));
