@@ -9,6 +9,7 @@
 
 #include "dg_euvac.h"
 #include "dg_internal.cuh"
+#include "dg_nvtx.h"
 #include "dg_map.cuh"
 
 namespace dg {
@@ -577,6 +578,7 @@ extern "C" int dg_mesh_set_interp(dg_mesh* mesh, int32_t mode) {
 }
 
 extern "C" int dg_gradient(dg_mesh* mesh, const double* u, double* q, void* stream) {
+  dg::NvtxRange nvtx_range_("dg_gradient");
   if (!mesh || !u || !q) return fail(DG_EINVAL, "dg_gradient: null argument");
   cudaStream_t s = (cudaStream_t)stream;
   int rc = drv_gradient(mesh, u, nullptr, s);
@@ -585,6 +587,7 @@ extern "C" int dg_gradient(dg_mesh* mesh, const double* u, double* q, void* stre
 }
 
 extern "C" int dg_residual(dg_mesh* mesh, const double* u, const double* q, double t, double* r, void* stream) {
+  dg::NvtxRange nvtx_range_("dg_residual");
   if (!mesh || !u || !r) return fail(DG_EINVAL, "dg_residual: null argument");
   cudaStream_t s = (cudaStream_t)stream;
   int rc;
@@ -637,6 +640,7 @@ __global__ void k_sumsq2(long long n, const double* __restrict__ x, const double
 
 extern "C" int dg_jvp(dg_mesh* mesh, const double* u, const double* v, double t, int32_t mode, double eps,
                       double* jv, double* r_out, void* stream) {
+  dg::NvtxRange nvtx_range_("dg_jvp");
   if (!mesh || !u || !v || !jv) return fail(DG_EINVAL, "dg_jvp: null argument");
   cudaStream_t s = (cudaStream_t)stream;
   if (mode == DG_JV_EXACT) {

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "dg_internal.cuh"
+#include "dg_nvtx.h"
 
 struct dg_radial;
 
@@ -1408,18 +1409,21 @@ extern "C" int dg_radial_sizes(const dg_radial* rad, int64_t* n_col, int32_t* n_
 }
 
 extern "C" int dg_radial_residual(dg_radial* rad, const double* u, double t, double* r, void* stream) {
+  dg::NvtxRange nvtx_range_("dg_radial_residual");
   if (!rad || !u || !r) return fail(DG_EINVAL, "dg_radial_residual: null argument");
   return residual_any(rad, u, nullptr, t, r, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int dg_radial_jvp(dg_radial* rad, const double* u, const double* v, double t, double* jv, double* r_out,
                              void* stream) {
+  dg::NvtxRange nvtx_range_("dg_radial_jvp");
   if (!rad || !u || !v || !jv) return fail(DG_EINVAL, "dg_radial_jvp: null argument");
   return residual_any(rad, u, v, t, r_out, jv, (cudaStream_t)stream);
 }
 
 extern "C" int dg_radial_step(dg_radial* rad, double* u, double t, double dt, int32_t stages, double newton_rtol,
                               int32_t max_newton, dg_radial_stats* stats, void* stream) {
+  dg::NvtxRange nvtx_range_("dg_radial_step");
   if (!rad || !u) return fail(DG_EINVAL, "dg_radial_step: null argument");
   if (stages < 1 || stages > 3 || !(dt > 0) || !(newton_rtol > 0) || max_newton < 1)
     return fail(DG_EINVAL, "dg_radial_step: need 1 <= stages <= 3, dt > 0, newton_rtol > 0, max_newton >= 1");

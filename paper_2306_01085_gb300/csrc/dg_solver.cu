@@ -17,6 +17,7 @@
 
 #include "dg_bits.cuh"
 #include "dg_internal.cuh"
+#include "dg_nvtx.h"
 
 namespace dg {
 
@@ -1824,6 +1825,7 @@ static int rb_build(dg_mesh* m, Solver* S, int kind, const double* U, double t, 
 
 // (re)build the preconditioner of kind at state U
 static int pc_setup(dg_mesh* m, Solver* S, int kind, const double* U, double t, double c, cudaStream_t s, bool f32) {
+  dg::NvtxRange nvtx_range_("preconditioner setup");
   S->lag_valid = false;   // a lagged preconditioner is only reused as its own step built it
   if (kind == DG_PC_BJ || kind == DG_PC_RB_BJ) return bj_setup(m, S, U, t, c, s, f32);
   if (kind == DG_PC_BJ16) return bj_setup(m, S, U, t, c, s, f32, true);
@@ -1837,6 +1839,7 @@ static int pc_setup(dg_mesh* m, Solver* S, int kind, const double* U, double t, 
 // x0_given: x holds an initial guess and the work vector VRES already holds b - J_G x
 static int gmres(dg_mesh* m, Solver* S, const dg_solver_opts& o, const double* U, double t, double c,
                  const double* b, double* x, int* iters, cudaStream_t s, bool x0_given = false) {
+  dg::NvtxRange nvtx_range_("GMRES");
   const long long n = S->n;
   const int R = o.gmres_restart;
   double* V = S->V;
@@ -2049,6 +2052,7 @@ extern "C" int dg_rb_reset(dg_mesh* mesh) {
 
 extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, const dg_solver_opts* opts,
                                 dg_step_stats* stats, void* stream) {
+  dg::NvtxRange nvtx_range_("dg_implicit_step");
   if (!mesh || !u || !opts) return fail(DG_EINVAL, "dg_implicit_step: null argument");
   const dg_solver_opts o = *opts;
   cudaStream_t s = (cudaStream_t)stream;
@@ -2115,6 +2119,7 @@ extern "C" int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, c
     }
   }
   for (int i = 0; i < o.stages; ++i) {
+    dg::NvtxRange stage_range("DIRK stage");
     const double ti = t + c[i] * dt, ci = dt * A[i][i];
     // known = M u_n + dt sum_{j<i} a_ij R_j
     rc = dg_mass_apply(mesh, un, Mun, s);

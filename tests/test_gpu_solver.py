@@ -223,6 +223,35 @@ def test_solver_variants_reach_the_same_state(torch_cuda):
     assert all(r[0]["status"] == 0 for r in runs.values())
 
 
+def test_resume_from_checkpoint_is_bit_identical(torch_cuda, tmp_path):
+    """Three DIRK(3,3) steps straight through, and two steps, a checkpoint, a new mesh built from
+    the checkpoint's description and one more step: the final states are bit for bit the same
+    (per-step block-Jacobi builds, FP32 inner Jv)."""
+    torch = torch_cuda
+    from paper_2306_01085_gb300 import checkpoint as CK
+    from paper_2306_01085_gb300.dg import Mesh
+    d = W.shell_desc(n=3, nr=4, p=2, euv=True)
+    dt = 60.0 / W.shell_reference().t0
+    kw = dict(stages=3, precond="bj16", jv_prec="f32")
+    m = Mesh(d)
+    u0 = torch.from_numpy(W.state_for(d, m.nodes().cpu().numpy(), 3)).cuda()
+    straight = u0.clone()
+    for k in range(3):
+        m.implicit_step(straight, k * dt, dt, **kw)
+    u = u0.clone()
+    for k in range(2):
+        m.implicit_step(u, k * dt, dt, **kw)
+    CK.save(tmp_path / "run.npz", d, u, 2 * dt, 2)
+    m.close()
+    c = CK.load(tmp_path / "run.npz")
+    m2 = Mesh(c["desc"])
+    u2 = torch.from_numpy(c["u"]).cuda()
+    m2.implicit_step(u2, c["t"], dt, **kw)
+    m2.close()
+    assert c["step"] == 2
+    assert torch.equal(u2, straight)
+
+
 def test_lagged_preconditioner_refresh(torch_cuda):
     """DG_REFRESH_LAGGED builds the FP16 block-Jacobi preconditioner on the first of every
     refresh_every steps and reuses it in between (no setup time on those steps); a change of dt or
