@@ -835,7 +835,7 @@ def main_precision(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     B.build()
-    config = args.config if args.config != CONFIG_NAME else "shell32x16_p2_euv"
+    config = args.config   # the benchmarked 12,288-element p = 4 shell unless --config says otherwise
     desc = W.CONFIGS[config][0]()
     mesh = DG.Mesh(desc)
     u = W.state_for(desc, mesh.nodes().cpu().numpy(), 2)
