@@ -136,8 +136,12 @@ __device__ __forceinline__ void wall1(const RPhys<R>& P, const S u[3], S ub[3]) 
   ub[2] = s_exp(R(0.5) * u[0]) * P.t_wall;
 }
 
+template <typename R> __device__ __forceinline__ R val_of(R x) { return x; }
+template <typename R> __device__ __forceinline__ R val_of(DualT<R> x) { return x.v; }
+
 // EUVAC heating q* (efficiency 1) at radius r above the site, Sec. 2.2 with Smith & Smith Chapman
-// depths for the single absorber (oxygen); zero in the Earth's shadow
+// depths for the single absorber (oxygen); zero in the Earth's shadow. Bands whose optical depth
+// exceeds 40 are skipped: their attenuated flux is below e^-40 (4e-18) of the band's own.
 template <typename S, typename R>
 __device__ __forceinline__ S heat1(const RPhys<R>& P, R r, const R site[3], R t, const S& isr, const S& T) {
   const R wt = P.omega_t * t;
@@ -156,10 +160,11 @@ __device__ __forceinline__ S heat1(const RPhys<R>& P, R r, const R site[3], R t,
   else ch = base * (R(2) * s_exp(rt * (R(1) - schi)) - ex);
   const S k = (P.cc * er) * Hs * ch;
   S qs = s_zero<S>();
+  const R kv = val_of(k);
 #pragma unroll 1
   for (int j = 0; j < P.n_euvac; ++j) {
     const R Phi = P.inv_m * P.phi[j];
-    qs = qs + (P.B[j] * Phi) * s_exp(-Phi * k);
+    if (Phi * kv < R(40)) qs = qs + (P.B[j] * Phi) * s_exp(-Phi * k);
   }
   return er * qs;
 }
