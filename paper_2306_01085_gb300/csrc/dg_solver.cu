@@ -126,7 +126,10 @@ __global__ void k_lincomb(long long n, double a, const double* x, double b, cons
 
 // out = x * (*scale_num) / sqrt(*scale_den)  (device-resident scalars)
 __global__ void k_scale_dev(long long n, const double* x, const double* __restrict__ den, double* out) {
-  const double s = 1.0 / sqrt(*den);
+  __shared__ double s_sh;   // the scale formed once per block (an FP64 square root and division)
+  if (threadIdx.x == 0) s_sh = 1.0 / sqrt(*den);
+  __syncthreads();
+  const double s = s_sh;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = x[i] * s;
 }
@@ -539,7 +542,10 @@ __global__ void __launch_bounds__(RED_THREADS, 2) k_update_dot_f32v(long long n2
 // out = a x in FP32 (a new basis vector), and the FP32 vector widened back to FP64
 __global__ void k_scale_to_f32(long long n, const double* __restrict__ x, double a, const double* __restrict__ den,
                                float* __restrict__ out) {
-  const float sf = den ? (float)(1.0 / sqrt(*den)) : (float)a;
+  __shared__ float sf_sh;   // the scale formed once per block
+  if (threadIdx.x == 0) sf_sh = den ? (float)(1.0 / sqrt(*den)) : (float)a;
+  __syncthreads();
+  const float sf = sf_sh;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = to_f32(x[i]) * sf;
 }
