@@ -151,9 +151,10 @@ int dg_mesh_nodes(const dg_mesh* mesh, double* x, void* stream);
  *   DG_INTERP_FP64: sum-factorised 1D passes in FP64 arithmetic on the CUDA cores;
  *   DG_INTERP_TC:   one dense contraction per element on the tensor cores (tcgen05, FP16 operands
  *                   with FP32 accumulation), FP64-accurate by error-free slicing: both operands
- *                   rounded to 47 bits relative to their row / column maximum and split into six
- *                   base-256 digits; digit products of level <= 5 accumulated exactly; the error is
- *                   below 1e-12 of each variable's largest nodal value in its element.
+ *                   rounded to 53 bits relative to their row / column maximum and split into seven
+ *                   digits (exact in FP16); digit products of level <= 7 accumulated exactly in
+ *                   FP32; the error is about 1e-15 of each variable's largest nodal value in its
+ *                   element (FP64 passes: about 2e-16). Slower than DG_INTERP_FP64 on GB300.
  * The mode applies to later calls on this mesh (not stream-ordered: set it between evaluations).
  * Errors: DG_EINVAL for an unknown mode.
  */
