@@ -331,8 +331,8 @@ int dg_implicit_step(dg_mesh* mesh, double* u, double t, double dt, const dg_sol
  * DG_PC_BJ: the exact diagonal block of every element (including the path through the
  * neighbours' LDG gradients) is computed column by column by block-diagonal tangent sweeps and
  * inverted in place in FP32 by Gauss-Jordan elimination with partial pivoting (one CTA per block in
- * shared memory when it fits; otherwise blocked by panels of 32 columns in global memory, each
- * panel's transform applied to the other columns as one rank-32 product), so that applying the
+ * shared memory when it fits; otherwise blocked by panels of 16 to 32 columns in global memory,
+ * each panel's transform applied to the other columns as one product of that rank), so that applying the
  * preconditioner is one coalesced dense product per element. Synchronises the stream.
  * DG_ENAN on a zero pivot.
  * DG_PC_BJ16: as DG_PC_BJ, then every column j of an inverse is divided by the power of two c_j
