@@ -32,3 +32,20 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["sample"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_implicit_summary_reports_chosen_and_lagged_against_plain():
+    """The default line's implicit object: the chosen variant's and the lagged variant's speed-ups
+    over the plain step come from the variants' own step times, kernels are left out."""
+    sys.path.insert(0, ROOT)
+    import bench
+    res = {"metric": "m", "config": "c", "n_dof": 10, "dt_s": 60.0, "steps": 3,
+           "variants": {"plain_bj": {"wall_s_per_step": [6.0, 6.0, 6.0], "kernels_last_step": {"k": 1}},
+                        "mixed_bj16": {"wall_s_per_step": [1.0, 1.0, 1.0], "kernels_last_step": {"k": 1}},
+                        "mixed_bj16_lag3": {"wall_s_per_step": [1.0, 0.7, 0.7], "kernels_last_step": {"k": 1}}},
+           "speedup_mixed_bj16_vs_plain_bj": 6.0, "speedup_mixed_bj16_lag3_vs_plain_bj": 7.5}
+    s = bench.implicit_summary(res, "mixed_bj16")
+    assert s["chosen"] == "mixed_bj16" and s["speedup_chosen_vs_plain"] == 6.0
+    assert s["speedup_lagged_vs_plain"] == 7.5
+    assert all("kernels_last_step" not in v for v in s["variants"].values())
+    assert "lagged" in bench.IMPLICIT_VARIANTS["mixed_bj16_lag3"]["precond_refresh"]
