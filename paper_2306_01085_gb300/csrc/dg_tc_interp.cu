@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   bool ok = true;          // this thread's waits all completed
   long long q = 0;         // stream position of the next slice to consume
+  long long landed = 0;    // thread 0: slices whose bulk copy it has seen complete (in order)
   uint32_t mma_phase = 0;
 
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int j = 0; j < TC_L; ++j, ++q) {
           const int b = (int)(q & 1);
           if (ok) ok = mbar_wait(smem_addr(&bar_full[b]), (uint32_t)((q >> 1) & 1));
+          if (ok) ++landed;
           if (ok) {
             const uint32_t abase = smem_addr(as + (size_t)b * S::ASLICE);
             for (int i = 0; i < TC_L && i + j < TC_LV; ++i) {
@@ -319,8 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (q >= 1 && loaded < n_slices) {
             const long long pq = q - 1;
             if (ok) ok = mbar_wait(smem_addr(&bar_empty[pq & 1]), (uint32_t)((pq >> 1) & 1));
-            if (ok) issue_load(loaded);
-            ++loaded;
+            if (ok) issue_load(loaded++);
           }
         }
         mma_commit(smem_addr(&bar_mma));
@@ -391,9 +392,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   }
   if (!ok) atomicOr(err, 1);
-  // the ring's outstanding loads (requested but never consumed) land before the CTA exits
+  // every bulk copy this CTA issued lands before it exits (after a failed wait, the ones not seen
+  // complete are waited for here, each wait bounded)
   if (t == 0) {
-    for (long long pq = q; pq < loaded; ++pq)
+    for (long long pq = landed; pq < loaded; ++pq)
       if (!mbar_wait(smem_addr(&bar_full[pq & 1]), (uint32_t)((pq >> 1) & 1))) atomicOr(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
