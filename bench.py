@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--implicit-config", default="shell32x16_p2_euv")
     ap.add_argument("--implicit-chosen", default="mixed_bj16")
     ap.add_argument("--implicit-steps", type=int, default=3)
+    ap.add_argument("--dt", type=float, default=60.0, help="--implicit: the DIRK step in seconds")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-procs", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--implicit", action="store_true",
@@ -610,8 +611,8 @@ IMPLICIT_VARIANTS = {
 }
 
 
-def implicit_variants(config, names, n_steps, clocks=None, mlp_steps=2, mlp_epochs=20):
-    """Wall time per implicit DIRK(3,3) step of 60 s for the solver variants (1 GPU), every variant
+def implicit_variants(config, names, n_steps, clocks=None, mlp_steps=2, mlp_epochs=20, dt_s=60.0):
+    """Wall time per implicit DIRK(3,3) step of dt_s seconds for the solver variants (1 GPU), every variant
     from the same state; final states compared with plain_bj. With clocks (a running ClockSampler)
     each variant's steps get their own clock summary."""
     import numpy as np
@@ -624,7 +625,7 @@ def implicit_variants(config, names, n_steps, clocks=None, mlp_steps=2, mlp_epoc
     desc = W.CONFIGS[config][0]()
     mesh = DG.Mesh(desc)
     u0 = torch.from_numpy(W.state_for(desc, mesh.nodes().cpu().numpy(), 2)).cuda()
-    dt = 60.0 / W.shell_reference().t0
+    dt = dt_s / W.shell_reference().t0
     results, finals = {}, {}
     training = None
     if "mixed_mlp" in names:
@@ -695,7 +696,7 @@ def implicit_variants(config, names, n_steps, clocks=None, mlp_steps=2, mlp_epoc
             if fin is not None and name != "plain_bj":
                 results[name]["final_diff_rel_to_change"] = (np.abs(fin - ref).max(axis=(0, 2)) / du).tolist()
     out = {"metric": "implicit DIRK(3,3) step wall time at Newton 1e-8", "unit": "s/step",
-           "config": f"{config}: {W.CONFIGS[config][1]}", "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "dt_s": 60.0,
+           "config": f"{config}: {W.CONFIGS[config][1]}", "n_elem": mesh.n_elem, "n_dof": mesh.n_dof, "dt_s": dt_s,
            "steps": n_steps, "warmup_steps": 1, "variants": results, "mlp_training": training}
     base = results.get("plain_bj", {}).get("wall_s_per_step")
     for name in names:
@@ -730,7 +731,7 @@ def main_implicit(args):
     clocks.start()
     time.sleep(0.2)
     out = implicit_variants(config, args.variants.split(","), args.steps, clocks=clocks,
-                            mlp_steps=args.mlp_steps, mlp_epochs=args.mlp_epochs)
+                            mlp_steps=args.mlp_steps, mlp_epochs=args.mlp_epochs, dt_s=args.dt)
     out["clocks_loaded_window"] = clocks.stop()
     print(json.dumps(out), flush=True)
 

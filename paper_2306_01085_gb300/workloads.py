@@ -232,6 +232,9 @@ CONFIGS = {
                            "transport and four-absorber EUVAC heating, June solstice"),
     "shell48x16_p3_euv": (lambda: shell_desc(n=48, nr=16, p=3, euv=True),
                           "cubed-sphere shell 6x48x48x16, p=3, EUV"),
+    "shell36x28_p3_euvac": (lambda: shell_desc(n=36, nr=28, p=3, euvac=True, day=79.0),
+                            "cubed-sphere shell 6x36x36x28, p=3, EUVAC heating with Chapman depths, March "
+                            "equinox (the paper's production mesh at k = 3: 217,728 elements, 69.7M DOF)"),
     "shell24x8_p3_euv": (lambda: shell_desc(n=24, nr=8, p=3, euv=True),
                          "cubed-sphere shell 6x24x24x8, p=3, EUV (small profiling case, 8.8M DOF)"),
     "shell8x4_p3_euv": (lambda: shell_desc(n=8, nr=4, p=3, euv=True),

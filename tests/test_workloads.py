@@ -16,6 +16,7 @@ from paper_2306_01085_gb300 import workloads as W
     ("shell32x16_p2_euvac", 98_304, 2, 13_271_040),
     ("shell32x16_p2_comp", 98_304, 2, 13_271_040),
     ("shell48x16_p3_euv", 221_184, 3, 70_778_880),
+    ("shell36x28_p3_euvac", 217_728, 3, 69_672_960),
 ])
 def test_workload_sizes(name, n_elem, p, n_dof):
     d = W.CONFIGS[name][0]()
