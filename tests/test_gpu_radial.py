@@ -1,6 +1,6 @@
 """The radial 1D ensemble on the GPU (dg_radial_* through the C ABI) against the radial oracle.
 
-Residual and exact Jv per variable to 1e-12 of the variable's largest oracle value, at p = 1, 2, 3
+Residual and exact Jv per variable to 1e-12 of the variable's largest oracle value, at p = 1 to 4
 (the paper's 28-element p = 2 column and smaller ones), for columns with different sites, EUV
 efficiencies and conductivity factors, with a ragged column count; columns are independent
 (permuting the parameters permutes the results bit for bit); the DIRK(2,2) step of 30 s reaches
@@ -40,7 +40,7 @@ def _err(got, ref):
     return np.abs(got - ref).max(axis=(1, 2, 3)) / np.abs(ref).max(axis=(1, 2, 3))
 
 
-@pytest.mark.parametrize("p,n_elem,n_col", [(2, 28, 7), (1, 12, 5), (3, 10, 33)])
+@pytest.mark.parametrize("p,n_elem,n_col", [(2, 28, 7), (1, 12, 5), (3, 10, 33), (4, 8, 37)])
 def test_residual_and_jv_match_oracle(torch_cuda, p, n_elem, n_col):
     torch = torch_cuda
     from paper_2306_01085_gb300.dg import Radial
@@ -94,14 +94,16 @@ def test_library_mesh_matches_the_workload_mesh(torch_cuda):
     assert np.all(_err(rb, ra) <= 1e-12)
 
 
-def test_dirk22_step_matches_oracle(torch_cuda):
-    """The paper's 1D time step (DIRK(2,2), 30 s) on the 28-element p = 2 column: the ensemble's
-    FP32-Jacobian Newton iteration and the oracle's exact Newton with a dense solve reach the same
-    stage solutions, to the Newton tolerance."""
+@pytest.mark.parametrize("p,n_elem", [(2, 28), (4, 8)])
+def test_dirk22_step_matches_oracle(torch_cuda, p, n_elem):
+    """The paper's 1D time step (DIRK(2,2), 30 s) on the 28-element p = 2 column (and a p = 4
+    column, whose band is 44 wide on each side): the ensemble's FP32-Jacobian Newton iteration and
+    the oracle's exact Newton with a dense solve reach the same stage solutions, to the Newton
+    tolerance."""
     torch = torch_cuda
     from paper_2306_01085_gb300.dg import Radial
     n_col = 3
-    d = W.radial_desc(n_col=n_col)
+    d = W.radial_desc(n_col=n_col, n_elem=n_elem, p=p)
     params = W.radial_params(n_col, seed=12)
     u = W.radial_state(d, seed=13)
     dt = 30.0 / W.shell_reference().t0
