@@ -259,3 +259,27 @@ def test_tc_interp_mode_is_validated(torch_cuda):
     with pytest.raises(DgError):
         m.set_interp("bf16")
     m.close()
+
+
+def test_tc_interp_in_the_implicit_step(torch_cuda):
+    """The plain FP64 implicit step with the tensor-core interpolation (the Krylov solve's
+    tangent-only interpolation writes the tangent planes) reaches the FP64-pass step to the Newton
+    tolerance."""
+    torch = torch_cuda
+    from paper_2306_01085_gb300.dg import Mesh
+    d = W.shell_desc(n=3, nr=2, p=2, euv=True)
+    d.h_first = 0.0
+    dt = 10.0 / W.shell_reference().t0
+    m = Mesh(d)
+    u0 = torch.from_numpy(W.state_for(d, m.nodes().cpu().numpy(), 6)).cuda()
+    out = {}
+    for mode in ("fp64", "tc"):
+        m.set_interp(mode)
+        u = u0.clone()
+        st = m.implicit_step(u, 0.0, dt, stages=3, precond="bj", newton_rtol=1e-10, gmres_rtol=1e-6)
+        assert st["status"] == 0
+        out[mode] = u.cpu().numpy()
+    m.close()
+    change = np.abs(out["fp64"] - u0.cpu().numpy()).max()
+    assert change > 1e-6
+    assert np.abs(out["tc"] - out["fp64"]).max() <= 1e-8 * change
